@@ -1,0 +1,180 @@
+/*
+ * wproj.h -- C ABI of libwproj.so: W-projection gridding, degridding and imaging on one
+ * NVIDIA B300 (sm_103a). After Lao et al. 2019, "Parallel Implementation of W-projection
+ * Wide-Field Imaging" (the gridding step of Sec. 2.1/2.2, the IFFT to the image in the
+ * Fig. 1 and Fig. 2 captions), with the W-projection kernel of the method that paper
+ * parallelises (Cornwell et al. 2008, cited in Sec. 1).
+ *
+ * Conventions (all calls):
+ *   - Every pointer documented "device" is CUDA device memory owned by the caller and must
+ *     stay valid until the work on `stream` completes. The context owns its kernel tables
+ *     and scratch. `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - Calls are asynchronous on `stream` unless documented otherwise; they return a
+ *     WP_* status and never throw. On failure wp_last_error() describes the cause. After
+ *     WP_ECUDA the context may hold partial results; other failures leave outputs untouched.
+ *   - A context is not thread-safe and its scratch is shared by its calls: issue calls on
+ *     one context from one host thread, on one stream at a time.
+ *   - Complex values are interleaved (re, im) float32 pairs ("float2"); arrays are C order.
+ *   - Units: uvw in metres, frequencies in Hz, cell size in radians, w in wavelengths.
+ *
+ * Notation: N grid size, delta cell, L = N delta, du = 1/L, Nw planes, S_p full support of
+ * plane p, os oversampling, M screen lattice, c = 299792458 m/s.
+ */
+#ifndef WPROJ_H
+#define WPROJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define WP_OK        0
+#define WP_EINVAL    1   /* bad argument or parameter (message says which) */
+#define WP_ENOMEM    2   /* device or host allocation failed */
+#define WP_ECUDA     3   /* a CUDA runtime or cuFFT call failed */
+#define WP_EOVERFLOW 4   /* a size exceeds a 32-bit index the kernels use */
+#define WP_ESTATE    5   /* call order: e.g. gridding before wp_make_wkernels */
+
+/* Kernel-table precision (stored precision; generation is always float64). */
+#define WP_TABLE_F32  0
+#define WP_TABLE_F16  1
+#define WP_TABLE_BF16 2
+
+/* wp_grid flags. */
+#define WP_ACCUMULATE      1  /* add into `grid` (and *sum_w, *n_dropped) instead of overwriting */
+#define WP_HERMITIAN_PAIRS 2  /* also grid each sample as W*conj(V) at -uvw */
+
+typedef struct wp_ctx wp_ctx;
+
+typedef struct wp_params {
+  int32_t n;            /* grid and image size N (even, 16 <= N <= 32768) */
+  double  cell_rad;     /* image cell size delta (rad); the field L = N*delta needs L/sqrt(2) < 1 */
+  int32_t n_w;          /* number of w-planes, >= 1 (Sec. 3.1 uses 23) */
+  double  w_max;        /* |w| of the last plane (wavelengths), > 0 when n_w > 1 */
+  int32_t support_min;  /* full support of plane 0, taps per axis (Sec. 3.1 uses 9) */
+  int32_t support_max;  /* full support of plane Nw-1; S_p = S_min + rint((S_max-S_min) p/(Nw-1)) */
+  int32_t oversample;   /* os, even, 2..64 */
+  int32_t screen_m;     /* odd screen lattice size M; 0 selects max(65, 4*support_max + 1) */
+  int32_t table_type;   /* WP_TABLE_* */
+  int32_t tile_x;       /* origin-tile width for binning (cells); 0 = default */
+  int32_t tile_y;       /* origin-tile height (cells); 0 = default */
+  int32_t device;       /* CUDA device ordinal */
+} wp_params;
+
+/* Creates a context: validates `p`, derives the per-plane supports and w values, computes
+ * the taper's Legendre coefficients on the host and its image-plane correction on the
+ * device, and allocates the tables. Synchronous. *out is NULL on failure. */
+int wp_create(wp_ctx** out, const wp_params* p);
+
+/* Frees everything the context owns (synchronises its device first). NULL is a no-op. */
+void wp_destroy(wp_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none). Valid until the next call.
+ * With ctx == NULL: the last wp_create failure of the calling thread. */
+const char* wp_last_error(const wp_ctx* ctx);
+
+/* Builds the oversampled W-kernel of every plane, in float64, then stores it in the
+ * table precision (W-projection kernel: the method of Cornwell et al. 2008, Sec. 1):
+ *   screen  s_p(l_k, m_q) = t(x_k) t(x_q) exp(2 pi i w_p (n - 1)),  n = sqrt(1 - l^2 - m^2)
+ *           j = k - (M-1)/2, l_k = j L/M, x_k = 2 j/M, t = PSWF psi_0(c = pi S_min/2) / psi_0(0)
+ *   kernel  K_p(dx, dy) = (1/nu) sum_{k,q} s_p exp(-2 pi i (dx j_k + dy j_q)/(os M)),
+ *           dx, dy in (-S_p os/2, S_p os/2], w_p = p w_max/(Nw-1),
+ *           nu = Re sum of plane 0's taps at whole-cell offsets (dx, dy = 0 mod os).
+ * Must precede wp_grid / wp_degrid. Errors: WP_ECUDA. */
+int wp_make_wkernels(wp_ctx* ctx, void* stream);
+
+/* Convolutional gridding (Sec. 2.1 gridding loop; Sec. 2.2: C_full^2 taps per visibility):
+ * for every kept visibility k of row r, channel c (and its Hermitian partner if flagged):
+ *   U = rint(u * kx_c), V = rint(v * kx_c), kx_c = (f_c/c) * (os * (N*delta))   [float64]
+ *   p = min(Nw-1, rint(|w| * kw_c)), kw_c = (f_c/c) * ((Nw-1)/w_max), conj = (w < 0)
+ *   X = U + (N/2) os, i0 = floor((X - S_p os/2)/os) + 1, ox = i0 os - X + S_p os/2 - 1
+ *   grid[j0+b][i0+a] += W V * K_p[b os + oy - S_p os/2 + 1][a os + ox - S_p os/2 + 1]
+ *     (K_p conjugated when conj), a, b in [0, S_p).
+ * A visibility is dropped (and counted) if its footprint leaves [0, N)^2 or its
+ * coordinates are not finite or |U|, |V| >= 2^30. The Hermitian partner uses -uvw and
+ * W conj(V). The visibilities are binned by (plane, footprint-origin tile) with a counting
+ * sort (histogram, exclusive prefix sum, scatter: the start-index construction of Eq. 6).
+ *   uvw      device [nrow][3] float64 metres        freq   device [nchan] float64 Hz
+ *   vis      device [nrow][nchan] float2            weight device [nrow][nchan] float32, or NULL (all 1)
+ *   grid     device [N][N] float2 (row = v, column = u); zeroed first unless WP_ACCUMULATE
+ *   sum_w    device float64, or NULL: receives (adds, with WP_ACCUMULATE) sum of kept weights
+ *   n_dropped device int64, or NULL: receives (adds) the number of dropped gridded visibilities
+ * Errors: WP_EINVAL (sizes, NULL pointers), WP_ESTATE (no kernels), WP_ENOMEM (scratch),
+ * WP_EOVERFLOW (more than 2^31 - 1 gridded visibilities), WP_ECUDA. */
+int wp_grid(wp_ctx* ctx, const double* uvw, const double* freq, const void* vis,
+            const float* weight, int64_t nrow, int32_t nchan, int32_t flags, void* grid,
+            double* sum_w, int64_t* n_dropped, void* stream);
+
+/* Degridding, the adjoint of wp_grid with unit weights (Sec. 2 names gridding and
+ * degridding as the pair being accelerated):
+ *   vis_out[r][c] = sum_{a,b} grid[j0+b][i0+a] * conj(K_k[...])   (same coordinates and taps;
+ *   K_k = K_p or conj(K_p) for w < 0); dropped visibilities get 0.
+ *   grid device [N][N] float2 (read only); vis_out device [nrow][nchan] float2 (overwritten).
+ * Errors as wp_grid. */
+int wp_degrid(wp_ctx* ctx, const double* uvw, const double* freq, const void* grid,
+              int64_t nrow, int32_t nchan, void* vis_out, void* stream);
+
+/* Dirty image from the grid (the IFFT of Fig. 1 / Fig. 2) with the taper correction:
+ *   I[j][i] = Re sum_{h,g} G[h][g] exp(+2 pi i ((g-N/2)(i-N/2) + (h-N/2)(j-N/2))/N)
+ *             / (sum_w * t(x_i) t(x_j)),  x_i = 2 (i - N/2)/N   (no t factor if !taper_correct)
+ *   grid  device [N][N] float2, CLOBBERED (used as the in-place FFT buffer)
+ *   sum_w device float64 (e.g. as written by wp_grid)
+ *   image device [N][N] float32 (row = m, column = l)
+ * Uses one cuFFT C2C plan owned by the context. Errors: WP_EINVAL, WP_ECUDA. */
+int wp_fft_to_image(wp_ctx* ctx, void* grid, const double* sum_w, int32_t taper_correct,
+                    float* image, void* stream);
+
+/* ---- inspection and tracing ---- */
+
+/* Per-plane full support S_p and w_p (host memory, Nw entries each). Synchronous. */
+int wp_plane_info(const wp_ctx* ctx, int32_t* support_out, double* w_out);
+
+/* The float64 coordinate step of wp_grid alone. For each gridded visibility
+ * (k = r*nchan + c, then the Hermitian partners at k + nrow*nchan if flagged) writes 8
+ * int32: U, V, plane, conj, keep, i0, j0, ox | (oy << 16).
+ *   out device [ngridded][8] int32. Errors: WP_EINVAL, WP_ECUDA. */
+int wp_coords(wp_ctx* ctx, const double* uvw, const double* freq, int64_t nrow, int32_t nchan,
+              int32_t flags, int32_t* out, void* stream);
+
+/* Copies plane p's kernel to HOST memory in the canonical layout [ey][ex], ey, ex in
+ * [0, S_p os), offset d = e - S_p os/2 + 1: as float64 pairs (which = 0: the float64
+ * table before storage) or as float32 pairs of the stored values (which = 1).
+ * cap = capacity of out in complex elements (>= (S_p os)^2). Synchronous. */
+int wp_wkernel_export(wp_ctx* ctx, int32_t plane, int32_t which, void* out_host, int64_t cap);
+
+/* Normalisation nu of the last wp_make_wkernels (host double). Synchronous. */
+int wp_wkernel_norm(wp_ctx* ctx, double* nu_out);
+
+/* Phases reported by wp_profile_read (index into its output arrays). */
+#define WP_PHASE_WKERNELS 0  /* wp_make_wkernels */
+#define WP_PHASE_PLAN     1  /* coordinates, histogram, prefix sum, scatter (wp_grid / wp_degrid) */
+#define WP_PHASE_GRID     2  /* the gridding kernel */
+#define WP_PHASE_DEGRID   3  /* the degridding kernel */
+#define WP_PHASE_FFT      4  /* cuFFT inverse transform */
+#define WP_PHASE_IMAGE    5  /* image epilogue (shift, sign, weight and taper division) */
+#define WP_NPHASES        6
+
+/* Tracing: with enable != 0 the context records a CUDA event pair on the call's stream
+ * around each phase of every later call, and counts its own kernel launches. Events are
+ * only recorded, never waited on, so enabling adds no synchronisation. */
+int wp_profile(wp_ctx* ctx, int32_t enable);
+
+/* Waits for the recorded events, then writes per phase (WP_NPHASES entries, host arrays)
+ * the summed elapsed milliseconds and the number of timed intervals since the last read,
+ * and the number of this library's kernel launches since the last read; resets all three.
+ * Any output pointer may be NULL. Synchronous. */
+int wp_profile_read(wp_ctx* ctx, double* ms_out, int32_t* count_out, int64_t* launches_out);
+
+/* Host only (no device needed): the taper t(x) = psi_0(c, x) / psi_0(c, 0) that
+ * wp_make_wkernels and wp_fft_to_image use, at n points |x| <= 1 (host arrays).
+ * psi_0 from its Legendre expansion (eigenvector of the prolate operator in the Legendre
+ * basis, Xiao, Rokhlin & Yarvin 2001). Errors: WP_EINVAL (c <= 0, |x| > 1, NULL). */
+int wp_taper_eval_host(double c, const double* x, int64_t n, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WPROJ_H */

@@ -1,0 +1,42 @@
+// Image formation after the inverse FFT (the IFFT step of the Fig. 1 / Fig. 2 captions of
+// Lao et al. 2019) and the taper correction.
+//
+// With F = unnormalised inverse DFT of the grid (cuFFT C2C, CUFFT_INVERSE, in place),
+// the centred transform of wproj.h is
+//     I[j][i] = (-1)^(i + j) Re F[(j + N/2) mod N][(i + N/2) mod N]
+// (for even N the (g - N/2)(i - N/2) phase splits into e^{2 pi i g i / N} (-1)^(g + i)
+// times a factor (-1)^(N/2) per axis, which cancels over two axes, and (-1)^g on the
+// input is a shift of the output by N/2). The epilogue also divides by the weight sum
+// and by t(x_i) t(x_j).
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace wp {
+
+namespace {
+
+__global__ void k_image_post(const float2* __restrict__ f, const double* __restrict__ sum_w,
+                             const double* __restrict__ taper, int32_t taper_correct, float* __restrict__ image,
+                             int32_t n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n) return;
+  const int h = n / 2;
+  const float v = f[(int64_t)((j + h) % n) * n + (i + h) % n].x;
+  double den = *sum_w;
+  if (taper_correct) den *= taper[i] * taper[j];
+  const float sgn = ((i + j) & 1) ? -1.f : 1.f;
+  image[(int64_t)j * n + i] = sgn * v * (float)(1.0 / den);
+}
+
+}  // namespace
+
+cudaError_t launch_image_post(const float2* spectrum, const double* sum_w, const double* taper_img,
+                              int32_t taper_correct, float* image, int32_t n, cudaStream_t s) {
+  dim3 grid((n + 255) / 256, n);
+  k_image_post<<<grid, 256, 0, s>>>(spectrum, sum_w, taper_img, taper_correct, image, n);
+  return cudaGetLastError();
+}
+
+}  // namespace wp

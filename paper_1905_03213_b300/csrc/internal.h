@@ -1,0 +1,136 @@
+// Internal declarations of libwproj (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/wproj.h"
+
+namespace wp {
+
+constexpr double kCLight = 299792458.0;
+constexpr double kCoordLimit = 1073741824.0;  // 2^30: |U|, |V| bound for the int32 path
+
+// Imaging geometry used by the coordinate and binning kernels (passed by value).
+struct Geometry {
+  int32_t n;            // N
+  int32_t os;           // oversampling
+  int32_t n_w;          // planes
+  int32_t tile_x, tile_y, ntx, nty;
+  int64_t ntiles;       // ntx * nty
+  double os_l;          // os * (N * cell)
+  double wscale;        // (Nw - 1) / w_max, 0 if Nw == 1
+  const int32_t* supp;  // [Nw] device
+};
+
+// One gridded (or degridded) visibility after binning: 16 bytes.
+//   x, y : W*V as float bits (gridding) or the caller-order index in x (degridding)
+//   z    : i0 | (j0 << 16)                      footprint origin
+//   w    : ox | (oy << 8) | (conj << 31)        oversample offsets, conjugate flag
+struct __align__(16) Record {
+  uint32_t x, y, z, w;
+};
+
+// Host-side PSWF: Legendre coefficients gamma_k (even k) of
+// t(x) = psi_0(c, x) / psi_0(c, 0) = sum_k gamma_k P_k(x).
+std::vector<double> pswf_legendre_coefficients(double c);
+
+// sum_i g[i] P_{2i}(x) for i < ncoef.
+__host__ __device__ inline double legendre_even_series(const double* g, int ncoef, double x) {
+  // Bonnet recurrence: P_{k+1} = ((2k+1) x P_k - k P_{k-1}) / (k+1)
+  double p_prev = 1.0, p = x, sum = g[0];
+  for (int k = 1; k < 2 * ncoef - 1; ++k) {
+    const double p_next = ((2.0 * k + 1.0) * x * p - k * p_prev) / (k + 1.0);
+    p_prev = p;
+    p = p_next;
+    if ((k + 1) % 2 == 0) sum += g[(k + 1) / 2] * p;
+  }
+  return sum;
+}
+
+struct DeviceBuffer {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace wp
+
+struct wp_ctx {
+  wp_params prm{};
+  int32_t m = 0;                       // screen lattice (odd)
+  int32_t nsm = 0;                     // SM count of the device
+  double taper_c = 0.0;
+  std::vector<int32_t> supp;           // S_p
+  std::vector<double> wplane;          // w_p
+  std::vector<int64_t> tab_off;        // element offset of plane p in the stored (grid-layout) table
+  std::vector<int64_t> tab64_off;      // element offset of plane p in the canonical float64 table
+  std::vector<int64_t> quad_off;       // element offset of plane p's quadrant table
+  int64_t tab_elems = 0, tab64_elems = 0, quad_elems = 0;
+  std::vector<double> legendre;        // taper coefficients (even degrees)
+
+  // device state owned by the context
+  double* d_legendre = nullptr;
+  double* d_taper_img = nullptr;       // [N] t(x_i), x_i = 2 (i - N/2) / N
+  double* d_taper_lat = nullptr;       // [(M+1)/2] t(x_j), j = 0 .. (M-1)/2
+  double* d_cos = nullptr;             // [os M] cos(2 pi r / (os M))
+  double2* d_screen = nullptr;         // [Nw][H][H] screen quadrant (j, j' >= 0)
+  double2* d_stage = nullptr;          // [Nw][H][Dmax] first-axis sums
+  double2* d_quad = nullptr;           // quadrant kernels, per plane [D_p][D_p], d >= 0
+  double2* d_tab64 = nullptr;          // canonical float64 tables
+  void* d_tab = nullptr;               // stored tables (grid layout)
+  int32_t* d_supp = nullptr;
+  double* d_wplane = nullptr;
+  int64_t* d_tab_off = nullptr;
+  int64_t* d_tab64_off = nullptr;
+  int64_t* d_quad_off = nullptr;
+  double* d_nu = nullptr;
+  bool have_kernels = false;
+
+  // binning
+  wp::Geometry geo{};
+  int64_t nbins = 0;
+  uint32_t* d_counts = nullptr;        // [nbins]
+  uint32_t* d_offsets = nullptr;       // [nbins + 1], exclusive prefix sums, total at the end
+  uint32_t* d_cursor = nullptr;        // [nbins]
+  uint32_t* d_partials = nullptr;      // scan partials
+  double* d_chan = nullptr;            // [max_chan][2]: kx_c, kw_c
+  int32_t max_chan = 0;
+  wp::DeviceBuffer records;
+  unsigned long long* d_dropped = nullptr;
+  double* d_wsum = nullptr;
+
+  cufftHandle fft = 0;
+  bool have_fft = false;
+  std::string err;
+
+  // tracing
+  bool profiling = false;
+  std::vector<cudaEvent_t> event_pool;  // free events
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> intervals;
+  int64_t launches = 0;                 // own kernel launches since the last read
+};
+
+namespace wp {
+// kernel tables (wkernels.cu)
+cudaError_t launch_make_wkernels(wp_ctx* ctx, cudaStream_t s);
+cudaError_t launch_taper_eval(const double* d_leg, int ncoef, double* out, int64_t n, int mode,
+                              int32_t param, cudaStream_t s);
+// coordinates and binning (plan.cu)
+cudaError_t launch_channel_factors(const double* freq, int32_t nchan, double os_l, double wscale,
+                                   double* d_chan, cudaStream_t s);
+cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const float* weight,
+                        int64_t nrow, int32_t nchan, bool pairs, bool for_degrid, cudaStream_t s);
+cudaError_t launch_coords(wp_ctx* ctx, const double* uvw, int64_t nrow, int32_t nchan, bool pairs,
+                          int32_t* out, cudaStream_t s);
+// gridding / degridding (grid.cu)
+cudaError_t launch_grid(wp_ctx* ctx, float2* grid, cudaStream_t s);
+cudaError_t launch_degrid(wp_ctx* ctx, const float2* grid, float2* vis_out, cudaStream_t s);
+// imaging (image.cu)
+cudaError_t launch_image_post(const float2* spectrum, const double* sum_w, const double* taper_img,
+                              int32_t taper_correct, float* image, int32_t n, cudaStream_t s);
+}  // namespace wp
