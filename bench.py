@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Benchmark of the W-projection hot path on one B300 (or N independent replicas).
+
+One step = one pass of the whole path over the workload, all on one CUDA stream:
+  make_wkernels (float64 kernel tables) -> grid (float64 coordinates, bin sort, gridding)
+  -> degrid (coordinates, bin sort, degridding of the same grid) -> fft_to_image (cuFFT +
+  taper-corrected image epilogue).
+Metric: gridded visibilities per second for the whole step (the tap-update rate and the
+per-phase rates are reported beside it). The workload ("fp32"): 128 antennas in a 5 km
+disk, 4 channels 1.0-1.4 GHz, 480 samples over 8 h, 15.6M samples gridded with their
+Hermitian conjugates = 31.2M gridded visibilities, 2048^2 grid at 1", 32 w-planes,
+support 8-16, oversampling 8; synthetic, seeded, generated on the GPU (inputs 0.4 GB,
+larger than the 126 MB L2, so no L2 flush between steps).
+
+--impl reference runs the float64 CPU oracle (the reference arm here) on a bounded sample
+of the same workload on the host cores.
+
+Multi-GPU (torchrun): every rank runs its own independent imaging job of the same size
+(independent problems shard with no collective); value = all ranks' visibilities / the
+max over ranks of the timed region; scaling "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "gridded visibilities/s (whole W-projection step: kernels, coordinates+sort, grid, degrid, FFT+taper)"
+WORKLOAD = ("fp32: 128 ants / 5 km, 4 ch 1.0-1.4 GHz, 480 samples / 8 h -> 15.6M samples + Hermitian "
+            "conjugates = 31.2M gridded vis; 2048^2 @ 1\", 32 w-planes, support 8-16, os 8")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def fp32_peak_tflops(nsm=148, mhz=2032.0):
+    """FP32 FMA peak from unit counts: SMs x 128 lanes x 2 flop x max SM clock."""
+    return nsm * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": float(max(power)) if power else None}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def run_gpu(args):
+    import torch
+    import synth
+    import paper_1905_03213_b300 as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = synth.config(args.config)
+    cfg.seed += 97 * rank                          # an independent job per rank
+    ob = synth.observe(cfg, device=f"cuda:{local}", rows=args.rows or None)
+    uvw, vis, wt = ob.uvw.contiguous(), ob.vis.contiguous(), ob.weight.contiguous()
+    freq = torch.as_tensor(ob.freqs, dtype=torch.float64, device=dev)
+    tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (0, 0)
+    wp = W.WProj(n=cfg.n, cell=cfg.cell, n_w=cfg.n_w, w_max=ob.w_max, support_min=cfg.s_min,
+                 support_max=cfg.s_max, oversample=cfg.oversample, table=args.table, tile=tile, device=local)
+    n = cfg.n
+    grid = torch.empty((n, n), dtype=torch.complex64, device=dev)
+    image = torch.empty((n, n), dtype=torch.float32, device=dev)
+    pred = torch.empty_like(vis)
+    sum_w = torch.zeros(1, dtype=torch.float64, device=dev)
+    ndrop = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def step():
+        wp.make_wkernels()
+        wp.grid(uvw, freq, vis, wt, grid=grid, sum_w=sum_w, n_dropped=ndrop, hermitian_pairs=cfg.hermitian_pairs)
+        wp.degrid(uvw, freq, grid, vis_out=pred)
+        wp.fft_to_image(grid, sum_w, image=image)
+
+    # untimed: the work counts (kept visibilities and taps) from the library's own coordinates
+    step()
+    torch.cuda.synchronize()
+    sup, _ = wp.plane_info()
+    sup_t = torch.as_tensor(sup, device=dev).long()
+    crd = wp.coords(uvw, freq, hermitian_pairs=cfg.hermitian_pairs)
+    keep = crd[:, 4].bool()
+    kept = int(keep.sum().item())
+    taps_grid = int((sup_t[crd[:, 2][keep].long()] ** 2).sum().item())
+    crd = wp.coords(uvw, freq, hermitian_pairs=False)
+    keep = crd[:, 4].bool()
+    kept_degrid = int(keep.sum().item())
+    taps_degrid = int((sup_t[crd[:, 2][keep].long()] ** 2).sum().item())
+    del crd, keep
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wp.profile(True)
+    wp.profile_read()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    phase_ms, phase_cnt, launches = wp.profile_read()
+    wp.profile(False)
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    e2e = None if args.no_e2e else run_e2e(wp, uvw, vis, wt, freq, grid, sum_w, ndrop, pred, image, cfg, args,
+                                           stream, kept * world)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return None
+
+    grid_ms = phase_ms["grid"] / max(1, phase_cnt["grid"])
+    degrid_ms = phase_ms["degrid"] / max(1, phase_cnt["degrid"])
+    peaks = measured_peaks()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_fp32 = fp32_peak_tflops(nsm)
+    achieved = 8.0 * taps_grid / (grid_ms * 1e-3) / 1e12
+    # algorithmic bytes of one gridding launch: every 16-byte record read once, the grid's
+    # 8-byte cells read and written once, the plane tables read once
+    tab_bytes = sum((int(s) * cfg.oversample) ** 2 * (8 if args.table == "f32" else 4) for s in sup)
+    alg_bytes = kept * 16 + 2 * 8 * n * n + tab_bytes
+    out = {
+        "metric": METRIC,
+        "value": kept * world / (ms_step * 1e-3),
+        "unit": "visibilities/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.table == "f32" else f"f32 ({args.table} tables)",
+        "data": "synthetic (seeded array/uvw/sky generators; values from 200 point sources + noise)",
+        "config": {"workload": WORKLOAD if not args.rows else f"{WORKLOAD}; first {args.rows} rows only",
+                   "table": args.table, "tile": args.tile or "default", "gridded_visibilities": kept,
+                   "degridded_visibilities": kept_degrid, "l2": "inputs (0.4 GB) larger than L2; no flush",
+                   "parallelism": f"{world} independent job(s)"},
+        "taps_per_s": (taps_grid + taps_degrid) * world / (ms_step * 1e-3),
+        "phases_ms": {k: phase_ms[k] / max(1, phase_cnt[k]) for k in phase_ms},
+        "grid_kernel": {"ms": grid_ms, "vis_per_s": kept / (grid_ms * 1e-3), "taps_per_s": taps_grid / (grid_ms * 1e-3),
+                        "taps": taps_grid},
+        "degrid_kernel": {"ms": degrid_ms, "vis_per_s": kept_degrid / (degrid_ms * 1e-3),
+                          "taps_per_s": taps_degrid / (degrid_ms * 1e-3), "taps": taps_degrid},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                     "frac": achieved / peak_fp32, "traffic": None,
+                     "kernel": "k_grid_v1 (gridding scatter, 8 flop per tap)",
+                     "peak_note": "FP32 FMA peak derived from unit counts (148 SMs x 128 lanes x 2 x 2.032 GHz)",
+                     "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / (grid_ms * 1e-3) / 1e9,
+                             "peak_gbs": peaks.get("hbm_gbs"), "peak_note": "of measured"}},
+        "clocks": clk.summary(),
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        cb = cpu_baseline(args)
+        cb.pop("seconds", None)
+        cb.pop("kept", None)
+        out["cpu_baseline"] = cb
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def run_e2e(wp, uvw, vis, wt, freq, grid, sum_w, ndrop, pred, image, cfg, args, stream, units):
+    """The same step through the public API from pinned host buffers (copies inside the timing)."""
+    import torch
+    n = cfg.n
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h_uvw, h_vis, h_wt = uvw.cpu().pin_memory(), vis.cpu().pin_memory(), wt.cpu().pin_memory()
+    h_freq = freq.cpu().pin_memory()
+    h_img = torch.empty((n, n), dtype=torch.float32).pin_memory()
+    d_uvw, d_vis, d_wt, d_freq = torch.empty_like(uvw), torch.empty_like(vis), torch.empty_like(wt), torch.empty_like(freq)
+
+    def e2e_step():
+        d_uvw.copy_(h_uvw, non_blocking=True)
+        d_freq.copy_(h_freq, non_blocking=True)
+        d_vis.copy_(h_vis, non_blocking=True)
+        d_wt.copy_(h_wt, non_blocking=True)
+        wp.make_wkernels()
+        wp.grid(d_uvw, d_freq, d_vis, d_wt, grid=grid, sum_w=sum_w, n_dropped=ndrop,
+                hermitian_pairs=cfg.hermitian_pairs)
+        wp.degrid(d_uvw, d_freq, grid, vis_out=pred)
+        wp.fft_to_image(grid, sum_w, image=image)
+        h_img.copy_(image, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    steps = max(2, args.steps // 2)
+    e0.record(stream)
+    for _ in range(steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    h2d = h_uvw.numel() * 8 + h_vis.numel() * 8 + h_wt.numel() * 4 + h_freq.numel() * 8
+    return {"value": units / (ms * 1e-3), "unit": "visibilities/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": h_img.numel() * 4, "ms_per_step": ms}
+
+
+def cpu_sample_rows(cfg, target_vis):
+    return max(1, min(cfg.n_rows, target_vis // len(cfg.freqs)))
+
+
+def cpu_baseline(args, rows=None):
+    """The float64 oracle on the host cores over a bounded sample of the workload (its first
+    `rows` rows = the first time samples of every baseline), the same step as on the GPU:
+    kernels, coordinates, gridding, degridding, image."""
+    import synth
+    import oracle
+    from oracle import wproj
+    cfg = synth.config(args.config)
+    rows = rows or cpu_sample_rows(cfg, args.cpu_vis)
+    ob = synth.observe(cfg, rows=rows)
+    # w_max of the full observation, so the planes match the GPU run
+    enu = synth.antenna_enu(cfg.n_ant, cfg.radius_m, cfg.height_m, np.random.default_rng(cfg.seed))
+    uvw_all = synth.uvw_metres(enu, synth.SITE_LAT, cfg.dec, synth.hour_angles(cfg.n_time, cfg.duration_h))
+    w_max = float(np.max(np.abs(uvw_all[:, 2])) * np.max(cfg.freqs) / synth.C_LIGHT)
+    prm = oracle.Params(cfg.n, cfg.cell, cfg.n_w, w_max, cfg.s_min, cfg.s_max, cfg.oversample)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = max(1, min(cores, 32))    # each OpenMP private float64 grid is 67 MB at 2048^2
+    t0 = time.perf_counter()
+    tabs, _ = oracle.wkernels(prm)
+    crd = oracle.coords(ob.uvw, ob.freqs, prm, hermitian_pairs=cfg.hermitian_pairs)
+    c = wproj.gridded_values(ob.vis, ob.weight, crd)
+    g = oracle.grid(crd, c, tabs, prm, threads=threads)
+    crd1 = oracle.coords(ob.uvw, ob.freqs, prm)
+    oracle.degrid(crd1, g, tabs, prm, threads=threads)
+    oracle.fft_to_image(g, max(oracle.sum_weights(ob.weight, crd), 1.0), prm)
+    dt = time.perf_counter() - t0
+    kept = int(crd["keep"].sum())
+    return {"value": kept / dt, "unit": "visibilities/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {rows} rows ({kept} gridded visibilities) of the workload, full step "
+                      f"(kernels, coordinates, grid, degrid, image), float64, {dt:.1f} s on {threads} of {cores} cores",
+            "seconds": dt, "kept": kept}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    import synth
+    cfg = synth.config(args.config)
+    rows = cpu_sample_rows(cfg, args.cpu_vis)
+    times, cb = [], None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(args, rows=rows)
+        if i >= args.warmup:
+            times.append(r["seconds"])
+            cb = r
+    ms = 1e3 * float(np.mean(times))
+    value = cb["kept"] / (ms * 1e-3)
+    cb = dict(cb)
+    cb.pop("seconds")
+    cb.pop("kept")
+    cb["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "visibilities/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "sample_rows": rows}, "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "visibilities/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wproj", choices=["wproj", "reference"])
+    ap.add_argument("--config", default="fp32")
+    ap.add_argument("--table", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--tile", default="", help="origin tile WxH, e.g. 64x32")
+    ap.add_argument("--cpu-vis", type=int, default=1_000_000, help="visibilities (rows x channels) in the CPU sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rows", type=int, default=0, help="use only the first ROWS rows (profiling captures)")
+    args = ap.parse_args()
+    if args.impl != "reference":
+        args.warmup = max(args.warmup, 3)
+    out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
