@@ -21,6 +21,12 @@ ARCMIN = math.pi / (180 * 60)
 TOL_IMAGE = {"f32": 1e-5, "f16": 1e-3, "bf16": 3e-3}
 
 
+def inner(a):
+    """The inner half of an image, |l|, |m| < L/4, where the taper is far from zero."""
+    n = a.shape[0]
+    return a[n // 4: 3 * n // 4, n // 4: 3 * n // 4]
+
+
 def peak_rel(a, ref):
     a = np.asarray(a)
     ref = np.asarray(ref)

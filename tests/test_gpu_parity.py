@@ -6,7 +6,8 @@ import pytest
 import oracle
 from oracle import wproj
 import synth
-from gpu_cases import (TOL_IMAGE, make_wproj, oracle_results, parity_case, peak_rel, random_case, to_dev)
+from gpu_cases import (TOL_IMAGE, inner, make_wproj, oracle_results, parity_case, peak_rel, random_case,
+                       to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -86,35 +87,48 @@ def test_wkernel_tables_reduced_precision(torch_cuda, table, tol):
 
 # ---------------------------------------------------------------- gridding + image
 def _grid_and_image(case, table="f32", tile=(0, 0)):
+    """Grid, then both images: (grid, corrected image, uncorrected image, sum_w, n_dropped)."""
     import torch
     wp = make_wproj(case, table=table, tile=tile)
     uvw, f, vis, wt = to_dev(case)
     g, sw, nd = wp.grid(uvw, f, vis, wt, hermitian_pairs=case.pairs)
     gh = g.cpu().numpy()
+    g2 = g.clone()
     img = wp.fft_to_image(g, sw).cpu().numpy()
+    raw = wp.fft_to_image(g2, sw, taper_correct=False).cpu().numpy()
     torch.cuda.synchronize()
-    return gh, img, float(sw.item()), int(nd.item())
+    return gh, img, raw, float(sw.item()), int(nd.item())
+
+
+def _image_errors(case, g_ref, sw_ref, img, raw):
+    """Image metric: peak-relative max error of the uncorrected image over all pixels and
+    of the taper-corrected image over the inner half (the corrected image divides by
+    t(x_i) t(x_j), ~1e-8 in the corners, which would amplify float32 rounding there)."""
+    ref = oracle.fft_to_image(g_ref, sw_ref, case.prm)
+    ref_raw = oracle.fft_to_image(g_ref, sw_ref, case.prm, taper_correct=False)
+    e_raw, rms_raw = peak_rel(raw, ref_raw)
+    e_cor, rms_cor = peak_rel(inner(img), inner(ref))
+    return max(e_raw, e_cor), (e_raw, rms_raw, e_cor, rms_cor)
 
 
 @pytest.mark.parametrize("pairs,weights", [(False, True), (True, False)])
 def test_grid_and_image_parity_config(torch_cuda, pairs, weights):
     case = parity_case(pairs=pairs, weights=weights)
     crd, g_ref, sw_ref = oracle_results(case)
-    g, img, sw, nd = _grid_and_image(case)
+    g, img, raw, sw, nd = _grid_and_image(case)
     assert nd == int((~crd["keep"]).sum())
     assert abs(sw - sw_ref) <= 1e-12 * sw_ref
     eg, _ = peak_rel(g, g_ref)
     assert eg < 1e-6, eg
-    img_ref = oracle.fft_to_image(g_ref, sw_ref, case.prm)
-    emax, erms = peak_rel(img, img_ref)
-    assert emax < TOL_IMAGE["f32"], (emax, erms)
+    emax, detail = _image_errors(case, g_ref, sw_ref, img, raw)
+    assert emax < TOL_IMAGE["f32"], detail
 
 
 @pytest.mark.parametrize("tile", [(8, 8), (16, 64), (64, 16), (128, 128)])
 def test_grid_tile_shapes(torch_cuda, tile):
     case = random_case(n=128, nrow=1500, nchan=2, s_min=5, s_max=12, n_w=7)
     crd, g_ref, sw_ref = oracle_results(case)
-    g, img, sw, nd = _grid_and_image(case, tile=tile)
+    g, img, raw, sw, nd = _grid_and_image(case, tile=tile)
     eg, _ = peak_rel(g, g_ref)
     assert eg < 1e-6, (tile, eg)
 
@@ -123,10 +137,9 @@ def test_grid_tile_shapes(torch_cuda, tile):
 def test_grid_reduced_precision_tables(torch_cuda, table):
     case = parity_case()
     crd, g_ref, sw_ref = oracle_results(case)
-    g, img, sw, nd = _grid_and_image(case, table=table)
-    img_ref = oracle.fft_to_image(g_ref, sw_ref, case.prm)
-    emax, erms = peak_rel(img, img_ref)
-    assert emax < TOL_IMAGE[table], (table, emax, erms)
+    g, img, raw, sw, nd = _grid_and_image(case, table=table)
+    emax, detail = _image_errors(case, g_ref, sw_ref, img, raw)
+    assert emax < TOL_IMAGE[table], (table, detail)
 
 
 def test_uncorrected_image(torch_cuda):
@@ -193,8 +206,8 @@ def test_single_visibility_and_small_grid(torch_cuda):
 def test_repeat_runs_agree(torch_cuda):
     """Float32 atomics merge in any order: two runs agree to rounding."""
     case = random_case(n=128, nrow=3000, nchan=2)
-    g1, _, _, _ = _grid_and_image(case)
-    g2, _, _, _ = _grid_and_image(case)
+    g1 = _grid_and_image(case)[0]
+    g2 = _grid_and_image(case)[0]
     eg, _ = peak_rel(g1, g2)
     assert eg < 1e-6
 
