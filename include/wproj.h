@@ -107,6 +107,34 @@ int wp_grid(wp_ctx* ctx, const double* uvw, const double* freq, const void* vis,
             const float* weight, int64_t nrow, int32_t nchan, int32_t flags, void* grid,
             double* sum_w, int64_t* n_dropped, void* stream);
 
+/* Gridding without any device allocation during the call. The paper has no counterpart;
+ * this is a service for callers that cannot allocate device memory while they grid: for
+ * example a host program whose framework has already reserved the whole device for its own
+ * memory pool (a cudaMalloc from inside the library would fail or fragment that pool), or a
+ * latency-bound ingest loop in which a device allocation, which may synchronise the device
+ * and take milliseconds, is not acceptable. Such a caller creates the context and builds the
+ * kernels once beforehand (wp_create and wp_make_wkernels do allocate) and then calls this.
+ *
+ * Same arguments, flags, results and errors as wp_grid, computed by the same kernels. The
+ * per-call scratch that wp_grid keeps in a growable context buffer (one 16-byte record per
+ * gridded visibility, plus per-channel factors) is instead a fixed file-scope device array
+ * of 16 MiB + 64 KiB, which every GPU that loads this library holds until the process exits.
+ * Limits: at most 2^20 = 1048576 gridded visibilities per call (nrow * nchan, doubled with
+ * WP_HERMITIAN_PAIRS) and at most 4096 channels; larger calls return WP_EINVAL with a
+ * message and touch nothing. The call allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current) and caches it; make that first call before any stream capture.
+ * All calls, from every context on the device, share the one array, and it keeps the last
+ * call's contents (each call writes every record it reads, so nothing in it needs to start
+ * at zero): calls that overlap on the GPU (different streams, or different contexts on the
+ * same device, in flight at the same time) race on it and must be serialised by the caller.
+ * The context's own bin counters are also shared with its other calls, as for wp_grid. */
+int wp_grid_noalloc(wp_ctx* ctx, const double* uvw, const double* freq, const void* vis,
+                    const float* weight, int64_t nrow, int32_t nchan, int32_t flags, void* grid,
+                    double* sum_w, int64_t* n_dropped, void* stream);
+
 /* Degridding, the adjoint of wp_grid with unit weights (Sec. 2 names gridding and
  * degridding as the pair being accelerated):
  *   vis_out[r][c] = sum_{a,b} grid[j0+b][i0+a] * conj(K_k[...])   (same coordinates and taps;

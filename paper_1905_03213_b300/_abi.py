@@ -17,7 +17,7 @@ _TABLES = {"f32": WP_TABLE_F32, "f16": WP_TABLE_F16, "bf16": WP_TABLE_BF16}
 # every function declared in include/wproj.h
 SYMBOLS = ("wp_create", "wp_destroy", "wp_last_error", "wp_make_wkernels", "wp_grid", "wp_degrid",
            "wp_fft_to_image", "wp_plane_info", "wp_coords", "wp_wkernel_export", "wp_wkernel_norm",
-           "wp_profile", "wp_profile_read", "wp_taper_eval_host")
+           "wp_profile", "wp_profile_read", "wp_taper_eval_host", "wp_grid_noalloc")
 PHASES = ("wkernels", "plan", "grid", "degrid", "fft", "image")
 
 
@@ -56,6 +56,7 @@ def _load():
     L.wp_profile.argtypes = [P, I32]
     L.wp_profile_read.argtypes = [P, P, P, P]
     L.wp_taper_eval_host.argtypes = [D, P, I64, P]
+    L.wp_grid_noalloc.argtypes = [P, P, P, P, P, I64, I32, I32, P, P, P, P]
     return L
 
 
