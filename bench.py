@@ -229,7 +229,7 @@ def run_gpu(args):
                           "taps_per_s": taps_degrid / (degrid_ms * 1e-3), "taps": taps_degrid},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                      "frac": achieved / peak_fp32, "traffic": None,
-                     "kernel": "k_grid_v1 (gridding scatter, 8 flop per tap)",
+                     "kernel": "k_grid_v2 (register-accumulating gridding scatter, 8 flop per tap)" if args.table == "f32" else "k_grid_v1 (gridding scatter, 8 flop per tap)",
                      "peak_note": "FP32 FMA peak derived from unit counts (148 SMs x 128 lanes x 2 x 2.032 GHz)",
                      "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / (grid_ms * 1e-3) / 1e9,
                              "peak_gbs": peaks.get("hbm_gbs"), "peak_note": "of measured"}},

@@ -1,4 +1,6 @@
-// Gridding and degridding over the binned records (baseline kernels).
+// Gridding and degridding over the binned records (baseline kernels). Gridding with float32
+// tables and supports up to 32 runs the register-accumulating kernel of grid2.cu instead;
+// this one covers the other cases.
 //
 // Gridding (Sec. 2.1/2.2 of Lao et al. 2019): every visibility adds c_k K_k(a, b) to the
 // S_p x S_p cells of its footprint. Degridding is the adjoint gather.
@@ -53,6 +55,25 @@ __device__ __forceinline__ int64_t find_bin(const uint32_t* __restrict__ offsets
   return lo;
 }
 
+// From `b` (offsets[b] <= pos) forward to the bin containing `pos`: galloping steps then
+// bisection, so runs of empty bins cost O(log) loads.
+__device__ __forceinline__ int64_t advance_bin(const uint32_t* __restrict__ offsets, int64_t b, int64_t nbins,
+                                               uint32_t pos) {
+  if (offsets[b + 1] > pos) return b;
+  int64_t lo = b + 1, step = 1;
+  while (lo + step < nbins && offsets[lo + step] <= pos) {
+    lo += step;
+    step <<= 1;
+  }
+  int64_t hi = min(lo + step, nbins);
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (offsets[mid] <= pos) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
@@ -69,7 +90,7 @@ __global__ void __launch_bounds__(kThreads) k_grid_v1(const Record* __restrict__
   int64_t b = find_bin(offsets, nbins, beg);
   uint32_t pos = beg;
   while (pos < end) {
-    while (offsets[b + 1] <= pos) ++b;
+    b = advance_bin(offsets, b, nbins, pos);
     const uint32_t seg_end = min(end, offsets[b + 1]);
     const int p = (int)(b / g.ntiles);
     const int64_t tile = b - (int64_t)p * g.ntiles;
@@ -91,7 +112,7 @@ __global__ void __launch_bounds__(kThreads) k_grid_v1(const Record* __restrict__
       const T* kb = tab + (int64_t)(oy * g.os + ox) * taps;
       for (int t = lane; t < taps; t += 32) {
         const int bb = t / s, aa = t - bb * s;
-        const float2 k = load_tap<T>(kb + t);
+        const float2 k = load_tap<T>(kb + aa * s + bb);
         const float ki = sg * k.y;
         float2* cell = &sub[(lj + bb) * pitch + li + aa];
         atomicAdd(&cell->x, cr * k.x - ci * ki);
@@ -122,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) k_degrid_v1(const Record* __restrict
   int64_t b = find_bin(offsets, nbins, beg);
   uint32_t pos = beg;
   while (pos < end) {
-    while (offsets[b + 1] <= pos) ++b;
+    b = advance_bin(offsets, b, nbins, pos);
     const uint32_t seg_end = min(end, offsets[b + 1]);
     const int p = (int)(b / g.ntiles);
     const int s = g.supp[p];
@@ -138,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) k_degrid_v1(const Record* __restrict
       float sr = 0.f, si = 0.f;
       for (int t = lane; t < taps; t += 32) {
         const int bb = t / s, aa = t - bb * s;
-        const float2 k = load_tap<T>(kb + t);
+        const float2 k = load_tap<T>(kb + aa * s + bb);
         const float ki = sg * k.y;
         const float2 v = __ldg(&grid[(int64_t)(j0 + bb) * g.n + i0 + aa]);
         sr += v.x * k.x - v.y * ki;
@@ -178,6 +199,9 @@ cudaError_t degrid_typed(wp_ctx* ctx, const float2* grid, float2* out, cudaStrea
 
 cudaError_t launch_grid(wp_ctx* ctx, float2* grid, cudaStream_t s) {
   ++ctx->launches;
+  bool used = false;
+  const cudaError_t e = launch_grid_v2(ctx, grid, s, &used);
+  if (e != cudaSuccess || used) return e;
   switch (ctx->prm.table_type) {
     case WP_TABLE_F16: return grid_typed<__half2>(ctx, grid, s);
     case WP_TABLE_BF16: return grid_typed<__nv_bfloat162>(ctx, grid, s);

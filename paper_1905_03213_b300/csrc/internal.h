@@ -98,6 +98,8 @@ struct wp_ctx {
   uint32_t* d_offsets = nullptr;       // [nbins + 1], exclusive prefix sums, total at the end
   uint32_t* d_cursor = nullptr;        // [nbins]
   uint32_t* d_partials = nullptr;      // scan partials
+  uint32_t* d_costoff = nullptr;       // [nbins + 1] exclusive prefix sums of per-bin work estimates
+  uint32_t* d_partials2 = nullptr;     // scan partials of the work estimates
   double* d_chan = nullptr;            // [max_chan][2]: kx_c, kw_c
   int32_t max_chan = 0;
   wp::DeviceBuffer records;
@@ -125,10 +127,14 @@ cudaError_t launch_channel_factors(const double* freq, int32_t nchan, double os_
                                    double* d_chan, cudaStream_t s);
 cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const float* weight,
                         int64_t nrow, int32_t nchan, bool pairs, bool for_degrid, cudaStream_t s);
+// per-bin work estimate (fixed cost per non-empty bin + records x (S_p^2 + per-record cost)), scanned
+cudaError_t launch_bin_costs(wp_ctx* ctx, cudaStream_t s);
 cudaError_t launch_coords(wp_ctx* ctx, const double* uvw, int64_t nrow, int32_t nchan, bool pairs,
                           int32_t* out, cudaStream_t s);
 // gridding / degridding (grid.cu)
 cudaError_t launch_grid(wp_ctx* ctx, float2* grid, cudaStream_t s);
+// register-accumulating gridding kernel (grid2.cu); *used = false when the geometry is outside its limits
+cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used);
 cudaError_t launch_degrid(wp_ctx* ctx, const float2* grid, float2* vis_out, cudaStream_t s);
 // imaging (image.cu)
 cudaError_t launch_image_post(const float2* spectrum, const double* sum_w, const double* taper_img,

@@ -263,6 +263,21 @@ __global__ void k_scan_finish(uint32_t* __restrict__ offsets, uint32_t* __restri
   if (i == 0) offsets[n] = partials[nparts];
 }
 
+// Work estimate of bin b in units of 64 tap-updates: a fixed part for every non-empty bin
+// (sub-grid merge, local sort, barriers) plus, per record, its S_p^2 taps and a record cost.
+constexpr uint32_t kBinFixedTaps = 8192;
+constexpr uint32_t kRecordTaps = 24;
+
+__global__ void k_bin_costs(const uint32_t* __restrict__ offsets, int64_t nbins, Geometry g,
+                            uint32_t* __restrict__ cost) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  const uint32_t cnt = offsets[b + 1] - offsets[b];
+  const int s = g.supp[b / g.ntiles];
+  const uint64_t taps = cnt ? (uint64_t)kBinFixedTaps + (uint64_t)cnt * (uint64_t)(s * s + kRecordTaps) : 0;
+  cost[b] = (uint32_t)((taps + 63) / 64);
+}
+
 __global__ void k_coords_out(const double* __restrict__ uvw, const double* __restrict__ chan, int64_t nvis,
                              int32_t nchan, int32_t pairs, Geometry g, int32_t* __restrict__ out) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nvis; k += (int64_t)gridDim.x * blockDim.x) {
@@ -324,6 +339,22 @@ cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const
     if ((e = cudaGetLastError())) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_bin_costs(wp_ctx* ctx, cudaStream_t s) {
+  cudaError_t e;
+  ctx->launches += 4;
+  const unsigned blocks = (unsigned)((ctx->nbins + 255) / 256);
+  k_bin_costs<<<blocks, 256, 0, s>>>(ctx->d_offsets, ctx->nbins, ctx->geo, ctx->d_counts);
+  if ((e = cudaGetLastError())) return e;
+  const int64_t tiles = (ctx->nbins + kScanTile - 1) / kScanTile;
+  k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(ctx->d_counts, ctx->nbins, ctx->d_costoff, ctx->d_partials2);
+  if ((e = cudaGetLastError())) return e;
+  k_scan_partials<<<1, kScanThreads, 0, s>>>(ctx->d_partials2, tiles);
+  if ((e = cudaGetLastError())) return e;
+  // finish into d_costoff; d_counts (holding the costs) serves as the unused cursor output
+  k_scan_finish<<<blocks, 256, 0, s>>>(ctx->d_costoff, ctx->d_counts, ctx->nbins, ctx->d_partials2, tiles);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_coords(wp_ctx* ctx, const double* uvw, int64_t nrow, int32_t nchan, bool pairs, int32_t* out,

@@ -145,7 +145,8 @@ __device__ __forceinline__ __nv_bfloat162 store_tap<__nv_bfloat162>(double re, d
 }
 
 // Full tables: canonical float64 [ey][ex] and the stored grid layout
-// tab[p] + ((oy*os + ox)*S + b)*S + a with ex = a os + ox, ey = b os + oy.
+// tab[p] + ((oy*os + ox)*S + a)*S + b with ex = a os + ox, ey = b os + oy (footprint row b
+// fastest: the lanes that hold consecutive rows read consecutive taps).
 template <class T>
 __global__ void k_tables(KernelGeo kg, const double2* __restrict__ quad, const double* __restrict__ nu,
                          const int64_t* __restrict__ tab64_off, double2* __restrict__ tab64, T* __restrict__ tab,
@@ -167,7 +168,7 @@ __global__ void k_tables(KernelGeo kg, const double2* __restrict__ quad, const d
   tab64[idx] = make_double2(re, im);
   const int a = ex / kg.os, ox = ex - a * kg.os;
   const int b = ey / kg.os, oy = ey - b * kg.os;
-  tab[kg.tab_off[p] + ((int64_t)(oy * kg.os + ox) * s + b) * s + a] = store_tap<T>(re, im);
+  tab[kg.tab_off[p] + ((int64_t)(oy * kg.os + ox) * s + a) * s + b] = store_tap<T>(re, im);
 }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }

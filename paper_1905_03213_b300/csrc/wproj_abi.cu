@@ -186,7 +186,7 @@ void wp_destroy(wp_ctx* ctx) {
                   ctx->d_stage,    ctx->d_quad,      ctx->d_tab64,     ctx->d_tab,      ctx->d_supp,
                   ctx->d_wplane,   ctx->d_tab_off,   ctx->d_tab64_off, ctx->d_quad_off, ctx->d_nu,
                   ctx->d_counts,   ctx->d_offsets,   ctx->d_cursor,    ctx->d_partials, ctx->d_chan,
-                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum};
+                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -224,8 +224,8 @@ int wp_create(wp_ctx** out, const wp_params* p) {
   wp_ctx* ctx = new (std::nothrow) wp_ctx();
   if (!ctx) return fail(nullptr, WP_ENOMEM, "host allocation failed");
   ctx->prm = q;
-  if (ctx->prm.tile_x == 0) ctx->prm.tile_x = 32;
-  if (ctx->prm.tile_y == 0) ctx->prm.tile_y = 32;
+  if (ctx->prm.tile_x == 0) ctx->prm.tile_x = 16;
+  if (ctx->prm.tile_y == 0) ctx->prm.tile_y = 16;
   ctx->m = q.screen_m ? q.screen_m : std::max(65, 4 * q.support_max + 1);
   auto bail = [&](int code, const std::string& msg) {
     g_create_error = msg;
@@ -302,6 +302,8 @@ int wp_create(wp_ctx** out, const wp_params* p) {
             dalloc(&ctx->d_offsets, (size_t)ctx->nbins + 1) == cudaSuccess &&
             dalloc(&ctx->d_cursor, (size_t)ctx->nbins) == cudaSuccess &&
             dalloc(&ctx->d_partials, (size_t)scan_tiles + 1) == cudaSuccess &&
+            dalloc(&ctx->d_costoff, (size_t)ctx->nbins + 1) == cudaSuccess &&
+            dalloc(&ctx->d_partials2, (size_t)scan_tiles + 1) == cudaSuccess &&
             dalloc(&ctx->d_dropped, 1) == cudaSuccess && dalloc(&ctx->d_wsum, 1) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -460,7 +462,7 @@ int wp_wkernel_export(wp_ctx* ctx, int32_t plane, int32_t which, void* out_host,
   for (int ey = 0; ey < e; ++ey) {
     for (int ex = 0; ex < e; ++ex) {
       const int a = ex / os, ox = ex % os, b = ey / os, oy = ey % os;
-      const size_t src = ((size_t)(oy * os + ox) * s + b) * s + a;
+      const size_t src = ((size_t)(oy * os + ox) * s + a) * s + b;
       float re, im;
       if (esz == 8) {
         std::memcpy(&re, &raw[8 * src], 4);
