@@ -264,9 +264,9 @@ __global__ void k_scan_finish(uint32_t* __restrict__ offsets, uint32_t* __restri
 }
 
 // Work estimate of bin b in units of 64 tap-updates: a fixed part for every non-empty bin
-// (sub-grid merge, local sort, barriers) plus, per record, its S_p^2 taps and a record cost.
-constexpr uint32_t kBinFixedTaps = 8192;
-constexpr uint32_t kRecordTaps = 24;
+// (segment set-up, local sort, barriers) plus, per record, its S_p^2 taps and a record cost.
+constexpr uint32_t kBinFixedTaps = 2048;
+constexpr uint32_t kRecordTaps = 32;
 
 __global__ void k_bin_costs(const uint32_t* __restrict__ offsets, int64_t nbins, Geometry g,
                             uint32_t* __restrict__ cost) {
