@@ -100,6 +100,7 @@ struct wp_ctx {
   uint32_t* d_partials = nullptr;      // scan partials
   uint32_t* d_costoff = nullptr;       // [nbins + 1] exclusive prefix sums of per-bin work estimates
   uint32_t* d_partials2 = nullptr;     // scan partials of the work estimates
+  uint32_t* d_work = nullptr;          // [2] work-unit counters of the gridding kernel (zero at rest)
   double* d_chan = nullptr;            // [max_chan][2]: kx_c, kw_c
   int32_t max_chan = 0;
   wp::DeviceBuffer records;

@@ -186,7 +186,7 @@ void wp_destroy(wp_ctx* ctx) {
                   ctx->d_stage,    ctx->d_quad,      ctx->d_tab64,     ctx->d_tab,      ctx->d_supp,
                   ctx->d_wplane,   ctx->d_tab_off,   ctx->d_tab64_off, ctx->d_quad_off, ctx->d_nu,
                   ctx->d_counts,   ctx->d_offsets,   ctx->d_cursor,    ctx->d_partials, ctx->d_chan,
-                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2};
+                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2, ctx->d_work};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -304,6 +304,7 @@ int wp_create(wp_ctx** out, const wp_params* p) {
             dalloc(&ctx->d_partials, (size_t)scan_tiles + 1) == cudaSuccess &&
             dalloc(&ctx->d_costoff, (size_t)ctx->nbins + 1) == cudaSuccess &&
             dalloc(&ctx->d_partials2, (size_t)scan_tiles + 1) == cudaSuccess &&
+            dalloc(&ctx->d_work, 2) == cudaSuccess && cudaMemset(ctx->d_work, 0, 2 * sizeof(uint32_t)) == cudaSuccess &&
             dalloc(&ctx->d_dropped, 1) == cudaSuccess && dalloc(&ctx->d_wsum, 1) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
