@@ -1,0 +1,270 @@
+// Register-holding degridding kernel (the hot path of wp_degrid).
+//
+// Degridding (Sec. 2.1 of Lao et al. 2019; the adjoint of gridding): visibility k is
+//   V_k = sum_{a,b} conj(K_k(a, b)) G(i0 + a, j0 + b),
+// with K_k = K_p for w >= 0 and conj(K_p) for w < 0. The organisation mirrors the gridding
+// kernel (grid2.cu): CTAs take work units of equal estimated work, counting-sort each chunk
+// of binned records by footprint origin in shared memory, and each warp walks a contiguous
+// piece of the sorted chunk with all 32 lanes on the same record.
+//
+//   * The grid region under the segment's footprints is staged in shared memory once per
+//     segment; lane (g, a) keeps the cells of its rows of footprint column a in registers
+//     (row pairs packed for f32x2 FMAs) and reloads them only when the origin changes.
+//   * Per record a lane multiplies its taps (the same planar table as gridding, 8-byte
+//     loads) with its cells into a partial sum; the partials of a batch of records are then
+//     reduced across the warp with a halving butterfly (about one shuffle per record and
+//     component), after which lane l holds visibility l of the batch and stores it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "warp_common.cuh"
+
+namespace wp {
+
+namespace {
+
+struct D2Args {
+  const Record* recs;
+  const uint32_t* offsets;
+  const uint32_t* costoff;  // [nbins + 1] prefix sums of per-bin work estimates
+  int64_t nbins;
+  Geometry g;
+  const float2* tab;        // stored tables (f32), layout [plane][oy*os+ox][a][b]
+  const int64_t* tab_off;
+  const float2* grid;
+  float2* out;              // visibilities in caller order (record x = caller index)
+  int smem_bytes;
+  int group_tiles;
+  int nunits;
+  uint32_t* work;           // [2]: next unit, finished CTAs (both zero between launches)
+};
+
+// Row pitch (float2 entries) of the staged grid region: the smallest p >= cols with p = 4
+// mod 8, so rows two apart fall in opposite halves of the 32 banks.
+__host__ __device__ constexpr int sub_pitch(int cols) { return cols + ((12 - cols % 8) % 8); }
+// Rows staged for support s: the tile rows plus every row a lane of the layout can address.
+__host__ __device__ constexpr int sub_rows(int tile_y, int s) { return tile_y + lay_groups(s) * lay_rows(s) - 1; }
+__host__ __device__ constexpr int sub_bytes(int tile_x, int tile_y, int group, int s) {
+  return sub_rows(tile_y, s) * sub_pitch(group * tile_x + s - 1) * 8;
+}
+
+// Butterfly over the warp: on entry every lane holds partials v[0..NB) of the batch's NB
+// records; on return v[0] of lane l is the warp total of record l mod NB.
+template <int NB>
+__device__ __forceinline__ void batch_reduce(float (&v)[NB], int lane) {
+  int n = NB;
+  if (NB == 16) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 16);
+  }
+#pragma unroll
+  for (int bit = NB / 2; bit >= 1; bit >>= 1) {
+    const bool upper = (lane & bit) != 0;
+#pragma unroll
+    for (int i = 0; i < bit; ++i) {
+      const float send = upper ? v[i] : v[i + bit];
+      const float keep = upper ? v[i + bit] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    }
+  }
+  (void)n;
+}
+
+// One warp degrids the decoded, sorted records [beg, end) of the chunk at byte offset rec_off
+// from the grid region staged at sub_off (pitch entries per row, origin (sx0, sy0)).
+template <int S>
+__device__ __forceinline__ void warp_degrid(int tab_off, int sub_off, int pitch, int sx0, int sy0, int rec_off,
+                                            int beg, int end, float2* __restrict__ out) {
+  using L = Lay<S>;
+  constexpr int NB = L::RP <= 2 ? 32 : 16;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / S, a = lane - g * S;
+  const int row0 = lane < L::NL ? g * L::R : 0;   // lanes beyond the layout read (zero-tap) cells of row 0
+  const unsigned char* tab = dyn_smem() + tab_off;
+  const float2* sub = (const float2*)(dyn_smem() + sub_off);
+  const uint4* drec = (const uint4*)(dyn_smem() + rec_off);
+  unsigned long long GR[L::RPA], GI[L::RPA], NGI[L::RPA];   // cells: re, im, -im of row pairs
+  float gtr = 0.f, gti = 0.f;
+#pragma unroll
+  for (int k = 0; k < L::RPA; ++k) GR[k] = GI[k] = NGI[k] = 0ull;
+  uint32_t cz = kNoOrigin;
+  for (int b0 = beg; b0 < end; b0 += NB) {
+    float pre[NB], pim[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      pre[r] = pim[r] = 0.f;
+      if (b0 + r < end) {                          // warp-uniform
+        const uint4 rec = drec[b0 + r];
+        Taps<S> tv;
+        tv.load(tab + (rec.w & 0x7fffffffu), lane);
+        if (rec.z != cz) {                         // warp-uniform: load the cells under the new origin
+          cz = rec.z;
+          const float2* c = sub + ((int)(rec.z >> 16) - sy0 + row0) * pitch + ((int)(rec.z & 0xffff) - sx0) + a;
+#pragma unroll
+          for (int k = 0; k < L::RP; ++k) {
+            const float2 c0 = c[(2 * k) * pitch], c1 = c[(2 * k + 1) * pitch];
+            GR[k] = pack2(c0.x, c1.x);
+            GI[k] = pack2(c0.y, c1.y);
+            NGI[k] = pack2(-c0.y, -c1.y);
+          }
+          if (L::RT) {
+            const float2 ct = c[(2 * L::RP) * pitch];
+            gtr = ct.x;
+            gti = ct.y;
+          }
+        }
+        // conj(K_k) = (kr, -ki) for w >= 0 and (kr, ki) for w < 0: ki' = sg ki
+        const float sg = (rec.w & 0x80000000u) ? 1.f : -1.f;
+        const unsigned long long SG = pack2(sg, sg);
+        unsigned long long PR = 0ull, PI = 0ull;
+#pragma unroll
+        for (int k = 0; k < L::RP; ++k) {
+          const unsigned long long kr = pack2(tv.r[k].x, tv.r[k].y);
+          const unsigned long long ki = fma2(pack2(tv.i[k].x, tv.i[k].y), SG, 0ull);
+          PR = fma2(kr, GR[k], PR);                // re: gr kr - gi ki'
+          PR = fma2(ki, NGI[k], PR);
+          PI = fma2(ki, GR[k], PI);                // im: gr ki' + gi kr
+          PI = fma2(kr, GI[k], PI);
+        }
+        float sr = lo_of(PR) + hi_of(PR), si = lo_of(PI) + hi_of(PI);
+        if (L::RT) {
+          const float kt = sg * tv.t.y;
+          sr = fmaf(gtr, tv.t.x, fmaf(-gti, kt, sr));
+          si = fmaf(gtr, kt, fmaf(gti, tv.t.x, si));
+        }
+        pre[r] = sr;
+        pim[r] = si;
+      }
+    }
+    batch_reduce<NB>(pre, lane);
+    batch_reduce<NB>(pim, lane);
+    if (lane < NB && b0 + lane < end) out[drec[b0 + lane].x] = make_float2(pre[0], pim[0]);
+  }
+}
+
+template <int S>
+__device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, int x0, int y0, int width,
+                                            uint32_t s0, uint32_t s1, int cap, int tab_off, int sub_off,
+                                            int rec_off) {
+  using L = Lay<S>;
+  if (stage) stage_table<S>(a.tab + a.tab_off[p], a.g.os, tab_off);
+  // the grid region under the segment's footprints (cells outside the grid read as zero)
+  const int cols = width + S - 1, rows = sub_rows(a.g.tile_y, S), pitch = sub_pitch(cols);
+  float2* sub = (float2*)(dyn_smem() + sub_off);
+  for (int i = threadIdx.x; i < rows * cols; i += kThreads) {
+    const int r = i / cols, c = i - r * cols;
+    const int gy = y0 + r, gx = x0 + c;
+    sub[r * pitch + c] = (gy < a.g.n && gx < a.g.n) ? __ldg(&a.grid[(int64_t)gy * a.g.n + gx]) : make_float2(0.f, 0.f);
+  }
+  const int keys = width * a.g.tile_y;
+  const int warp = threadIdx.x >> 5;
+  for (uint32_t c0 = s0; c0 < s1; c0 += (uint32_t)cap) {
+    const int m = (int)min((uint32_t)cap, s1 - c0);
+    sort_chunk<S>((const uint4*)a.recs, c0, m, x0, y0, width, keys, a.g.os, rec_off);
+    const int beg = (int)((int64_t)m * warp / kWarps), end = (int)((int64_t)m * (warp + 1) / kWarps);
+    warp_degrid<S>(tab_off, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
+    __syncthreads();
+  }
+  (void)L::R;
+}
+
+__device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
+  int64_t bin = find_bin(a.offsets, a.nbins, beg);
+  uint32_t pos = beg;
+  int cur_plane = -1;
+  const int tab_off = kCountsBytes;
+  while (pos < end) {
+    bin = advance_bin(a.offsets, bin, a.nbins, pos);
+    const int p = (int)(bin / a.g.ntiles);
+    const int64_t tile = bin - (int64_t)p * a.g.ntiles;
+    const int ty = (int)(tile / a.g.ntx), tx = (int)(tile - (int64_t)ty * a.g.ntx);
+    const int s = a.g.supp[p];
+    const int sub_off = tab_off + a.g.os * a.g.os * lay_class_bytes(s);
+    const int rec_off = sub_off + sub_bytes(a.g.tile_x, a.g.tile_y, a.group_tiles, s);
+    const int cap = (a.smem_bytes - rec_off) / (int)sizeof(Record);
+    int ntiles = 1;
+    const uint32_t seg_end = segment_end(a.offsets, a.nbins, bin, tx, a.g.ntx, pos, end, cap, a.group_tiles, &ntiles);
+    const bool stage = p != cur_plane;
+    cur_plane = p;
+    const int x0 = tx * a.g.tile_x, y0 = ty * a.g.tile_y;
+    const int width = ntiles * a.g.tile_x;
+    switch (s) {
+#define WP_SEG_CASE(N)                                                                                   \
+  case N:                                                                                                \
+    degrid_segment<N>(a, p, stage, x0, y0, width, pos, seg_end, cap, tab_off, sub_off, rec_off);         \
+    break;
+      WP_SEG_CASE(1) WP_SEG_CASE(2) WP_SEG_CASE(3) WP_SEG_CASE(4) WP_SEG_CASE(5) WP_SEG_CASE(6) WP_SEG_CASE(7)
+      WP_SEG_CASE(8) WP_SEG_CASE(9) WP_SEG_CASE(10) WP_SEG_CASE(11) WP_SEG_CASE(12) WP_SEG_CASE(13)
+      WP_SEG_CASE(14) WP_SEG_CASE(15) WP_SEG_CASE(16)
+#undef WP_SEG_CASE
+      default:
+        break;
+    }
+    pos = seg_end;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_degrid_v2(D2Args a) {
+  for_each_unit(a.offsets, a.costoff, a.nbins, a.nunits, a.work,
+                [&](uint32_t beg, uint32_t end) { degrid_range(a, beg, end); });
+}
+
+}  // namespace
+
+// Dynamic shared memory of the launch, or 0 when the geometry is outside the kernel's limits
+// (then the baseline kernel of grid.cu runs).
+size_t degrid_v2_smem(const wp_ctx* ctx, int* group_tiles) {
+  const int smax = *std::max_element(ctx->supp.begin(), ctx->supp.end());
+  if (smax > kMaxS || ctx->prm.table_type != WP_TABLE_F32) return 0;
+  const int os = ctx->prm.oversample;
+  const int tx = ctx->geo.tile_x, ty = ctx->geo.tile_y;
+  if ((int64_t)tx * ty > kMaxKeys) return 0;
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->prm.device) != cudaSuccess)
+    return 0;
+  const size_t bytes = (size_t)optin - 1024;
+  int group = std::max(1, std::min(8, kMaxKeys / (tx * ty)));
+  // narrow the segment groups until every plane's table, grid region and a minimal chunk fit
+  for (; group >= 1; --group) {
+    bool fits = true;
+    for (int sp : ctx->supp) {
+      const size_t need = (size_t)kCountsBytes + (size_t)os * os * lay_class_bytes(sp) +
+                          (size_t)sub_bytes(tx, ty, group, sp) + (size_t)kMinChunk * sizeof(Record);
+      if (need > bytes) fits = false;
+    }
+    if (fits) break;
+  }
+  if (group < 1) return 0;
+  *group_tiles = group;
+  return bytes;
+}
+
+cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* out, cudaStream_t s, bool* used) {
+  int group = 1;
+  const size_t smem = degrid_v2_smem(ctx, &group);
+  *used = smem != 0;
+  if (!smem) return cudaSuccess;
+  D2Args a;
+  a.recs = (const Record*)ctx->records.ptr;
+  a.offsets = ctx->d_offsets;
+  a.costoff = ctx->d_costoff;
+  a.nbins = ctx->nbins;
+  a.g = ctx->geo;
+  a.tab = (const float2*)ctx->d_tab;
+  a.tab_off = ctx->d_tab_off;
+  a.grid = grid;
+  a.out = out;
+  a.smem_bytes = (int)smem;
+  a.group_tiles = group;
+  a.nunits = ctx->nsm * kUnitsPerCta;
+  a.work = ctx->d_work + 2;
+  cudaError_t e;
+  if ((e = launch_bin_costs(ctx, s))) return e;
+  if ((e = cudaFuncSetAttribute(k_degrid_v2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+  k_degrid_v2<<<ctx->nsm, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace wp

@@ -211,6 +211,9 @@ cudaError_t launch_grid(wp_ctx* ctx, float2* grid, cudaStream_t s) {
 
 cudaError_t launch_degrid(wp_ctx* ctx, const float2* grid, float2* out, cudaStream_t s) {
   ++ctx->launches;
+  bool used = false;
+  const cudaError_t e = launch_degrid_v2(ctx, grid, out, s, &used);
+  if (e != cudaSuccess || used) return e;
   switch (ctx->prm.table_type) {
     case WP_TABLE_F16: return degrid_typed<__half2>(ctx, grid, out, s);
     case WP_TABLE_BF16: return degrid_typed<__nv_bfloat162>(ctx, grid, out, s);

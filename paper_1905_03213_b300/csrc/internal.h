@@ -100,7 +100,7 @@ struct wp_ctx {
   uint32_t* d_partials = nullptr;      // scan partials
   uint32_t* d_costoff = nullptr;       // [nbins + 1] exclusive prefix sums of per-bin work estimates
   uint32_t* d_partials2 = nullptr;     // scan partials of the work estimates
-  uint32_t* d_work = nullptr;          // [2] work-unit counters of the gridding kernel (zero at rest)
+  uint32_t* d_work = nullptr;          // [4] work-unit counters: gridding [0..1], degridding [2..3] (zero at rest)
   double* d_chan = nullptr;            // [max_chan][2]: kx_c, kw_c
   int32_t max_chan = 0;
   wp::DeviceBuffer records;
@@ -137,6 +137,8 @@ cudaError_t launch_grid(wp_ctx* ctx, float2* grid, cudaStream_t s);
 // register-accumulating gridding kernel (grid2.cu); *used = false when the geometry is outside its limits
 cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used);
 cudaError_t launch_degrid(wp_ctx* ctx, const float2* grid, float2* vis_out, cudaStream_t s);
+// register-holding degridding kernel (degrid2.cu); *used = false when the geometry is outside its limits
+cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* vis_out, cudaStream_t s, bool* used);
 // imaging (image.cu)
 cudaError_t launch_image_post(const float2* spectrum, const double* sum_w, const double* taper_img,
                               int32_t taper_correct, float* image, int32_t n, cudaStream_t s);

@@ -1,0 +1,283 @@
+// Device code shared by the warp-synchronous gridding (grid2.cu) and degridding (degrid2.cu)
+// kernels: the lane layout of a footprint over a warp, the staged kernel-table layout, the
+// in-CTA counting sort of binned records by footprint origin, the segment walk over the
+// (plane, tile) bins and the work-unit schedule. Included by exactly those two files; every
+// definition has internal linkage.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace wp {
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxS = 16;                                     // larger supports: baseline kernel
+constexpr int kMaxKeys = 4096;                                  // origins of one segment
+constexpr int kCountsBytes = ((kMaxKeys + 1) * 4 + 15) & ~15;  // shared-memory counters
+constexpr int kMinChunk = 512;
+constexpr uint32_t kNoOrigin = 0xffffffffu;
+constexpr int kUnitsPerCta = 8;                              // work units per CTA, on average
+
+
+// Lane layout for support S: G row groups of S lanes; lane g*S + a holds rows g*R ..
+// g*R + R - 1 of footprint column a, as RP row pairs and RT (0/1) single tail row. The staged
+// table of one oversampling class holds, per row pair k, a block of 32 float2 {kr(2k), kr(2k+1)}
+// then a block of 32 float2 {ki(2k), ki(2k+1)} (one entry per lane), then for the tail row a
+// block of 32 float2 {kr, ki}. Lanes beyond G*S have all-zero entries.
+__host__ __device__ constexpr int lay_rows(int s) { return (s + 32 / s - 1) / (32 / s); }
+__host__ __device__ constexpr int lay_groups(int s) { return (s + lay_rows(s) - 1) / lay_rows(s); }
+// staged bytes per oversampling class: 2 RP blocks of 32 x float2, then one more if RT
+__host__ __device__ constexpr int lay_class_bytes(int s) { return (lay_rows(s) / 2) * 512 + (lay_rows(s) & 1) * 256; }
+
+template <int S>
+struct Lay {
+  static constexpr int R = lay_rows(S), G = lay_groups(S), NL = G * S;
+  static constexpr int RP = R / 2, RT = R & 1, RPA = RP > 0 ? RP : 1;
+  static constexpr int CB = lay_class_bytes(S);
+};
+
+__device__ __forceinline__ unsigned char* dyn_smem() {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  return smem_raw;
+}
+
+__device__ __forceinline__ int64_t find_bin(const uint32_t* __restrict__ offsets, int64_t nbins, uint32_t pos) {
+  int64_t lo = 0, hi = nbins;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (offsets[mid] <= pos) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// The bin containing record `pos`, searching forward from `bin` (offsets[bin] <= pos):
+// galloping steps of 1, 2, 4, ... then bisection, so long runs of empty bins cost O(log).
+__device__ __forceinline__ int64_t advance_bin(const uint32_t* __restrict__ offsets, int64_t bin, int64_t nbins,
+                                               uint32_t pos) {
+  if (offsets[bin + 1] > pos) return bin;
+  int64_t lo = bin + 1, step = 1;                 // offsets[lo] <= pos; offsets[nbins] > pos
+  while (lo + step < nbins && offsets[lo + step] <= pos) {
+    lo += step;
+    step <<= 1;
+  }
+  int64_t hi = min(lo + step, nbins);             // offsets[hi] > pos
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (offsets[mid] <= pos) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// In-place exclusive scan of the shared counters counts[0..n) by the whole block.
+__device__ void block_exclusive_scan(int n) {
+  __shared__ uint32_t warp_sums[kWarps];
+  uint32_t* counts = (uint32_t*)dyn_smem();
+  const int per = (n + kThreads - 1) / kThreads;
+  const int beg = threadIdx.x * per;
+  uint32_t local = 0;
+  for (int i = 0; i < per; ++i)
+    if (beg + i < n) local += counts[beg + i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = local;
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t s = lane < kWarps ? warp_sums[lane] : 0u;
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, s, off);
+      if (lane >= off) s += y;
+    }
+    if (lane < kWarps) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  uint32_t run = (warp ? warp_sums[warp - 1] : 0u) + x - local;
+  for (int i = 0; i < per; ++i) {
+    if (beg + i < n) {
+      const uint32_t v = counts[beg + i];
+      counts[beg + i] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+}
+
+// Packed pair of floats (two footprint rows) as one 64-bit register for fma.rn.f32x2.
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+  return (unsigned long long)__float_as_uint(a) | ((unsigned long long)__float_as_uint(b) << 32);
+}
+__device__ __forceinline__ float lo_of(unsigned long long v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi_of(unsigned long long v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long shfl_down2(unsigned long long v, int d) {
+  const uint32_t lo = __shfl_down_sync(0xffffffffu, (uint32_t)v, d);
+  const uint32_t hi = __shfl_down_sync(0xffffffffu, (uint32_t)(v >> 32), d);
+  return (unsigned long long)lo | ((unsigned long long)hi << 32);
+}
+
+// This lane's taps of one record: RP row pairs as {kr(2k), kr(2k+1)} and {ki(2k), ki(2k+1)}, and the tail.
+template <int S>
+struct Taps {
+  float2 r[Lay<S>::RPA], i[Lay<S>::RPA];
+  float2 t;
+  // Lanes beyond the layout (lane >= NL) read their all-zero table entries.
+  __device__ __forceinline__ void load(const unsigned char* cls_base, int lane) {
+    using L = Lay<S>;
+#pragma unroll
+    for (int k = 0; k < L::RP; ++k) {
+      r[k] = *(const float2*)(cls_base + k * 512 + lane * 8);
+      i[k] = *(const float2*)(cls_base + k * 512 + 256 + lane * 8);
+    }
+    if (L::RT) t = *(const float2*)(cls_base + L::RP * 512 + lane * 8);
+  }
+};
+
+// Stages one plane's table (src: layout [oy*os+ox][a][b]) in the lane layout of Lay<S> at
+// byte offset tab_off of the dynamic shared memory.
+template <int S>
+__device__ __forceinline__ void stage_table(const float2* __restrict__ src, int os, int tab_off) {
+  using L = Lay<S>;
+  constexpr int kPer = L::RP + L::RT;           // entries per lane and class
+  const int ncls = os * os;
+  unsigned char* dst = dyn_smem() + tab_off;
+  for (int i = threadIdx.x; i < ncls * 32 * kPer; i += kThreads) {
+    const int cls = i / (32 * kPer), rem = i - cls * (32 * kPer);
+    const int k = rem >> 5, lane = rem & 31;
+    const int g = lane / S, col = lane - g * S;
+    const bool active = lane < L::NL;
+    const int b0 = g * L::R + 2 * k;
+    const float2* s = src + ((int64_t)cls * S + col) * S;
+    const float2 v0 = (active && b0 < S) ? __ldg(s + b0) : make_float2(0.f, 0.f);
+    unsigned char* d = dst + cls * L::CB + k * 512 + lane * 8;
+    if (k < L::RP) {
+      const float2 v1 = (active && b0 + 1 < S) ? __ldg(s + b0 + 1) : make_float2(0.f, 0.f);
+      *(float2*)d = make_float2(v0.x, v1.x);
+      *(float2*)(d + 256) = make_float2(v0.y, v1.y);
+    } else {
+      *(float2*)d = v0;
+    }
+  }
+}
+
+// Counting-sorts the binned records grecs[c0, c0 + m) of one segment (origin tiles of one
+// tile row, columns x0 .. x0 + width, rows y0 .. y0 + tile_y) by origin key (row-major within
+// the segment) into the shared array at byte offset rec_off, decoding each into
+//   x, y : as binned;  z : i0 | j0 << 16;  w : class byte offset in the staged table | conj << 31.
+// On return counts[key] (the shared counters at offset 0) is the end of the key's records.
+template <int S>
+__device__ __forceinline__ void sort_chunk(const uint4* __restrict__ grecs, uint32_t c0, int m, int x0, int y0,
+                                           int width, int keys, int os, int rec_off) {
+  using L = Lay<S>;
+  uint32_t* counts = (uint32_t*)dyn_smem();
+  uint4* drec = (uint4*)(dyn_smem() + rec_off);
+  for (int k = threadIdx.x; k < keys; k += kThreads) counts[k] = 0u;
+  __syncthreads();
+  // pass 1: histogram of the origin keys, 4 loads in flight
+  for (int r0 = threadIdx.x; r0 < m; r0 += 4 * kThreads) {
+    uint32_t z[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) z[u] = r0 + u * kThreads < m ? __ldcg(&grecs[c0 + r0 + u * kThreads].z) : kNoOrigin;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (z[u] != kNoOrigin) atomicAdd(&counts[((int)(z[u] >> 16) - y0) * width + ((int)(z[u] & 0xffff) - x0)], 1u);
+  }
+  __syncthreads();
+  block_exclusive_scan(keys);
+  // pass 2: decode each record into its sorted slot
+  for (int r0 = threadIdx.x; r0 < m; r0 += 4 * kThreads) {
+    uint4 rec[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (r0 + u * kThreads < m) rec[u] = __ldcs(grecs + c0 + r0 + u * kThreads);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (r0 + u * kThreads < m) {
+        const int key = ((int)(rec[u].z >> 16) - y0) * width + ((int)(rec[u].z & 0xffff) - x0);
+        const int cls = (int)((rec[u].w >> 8) & 0xff) * os + (int)(rec[u].w & 0xff);
+        const uint32_t w = (uint32_t)(cls * L::CB) | (rec[u].w & 0x80000000u);
+        drec[atomicAdd(&counts[key], 1u)] = make_uint4(rec[u].x, rec[u].y, rec[u].z, w);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// The segment starting at record `pos` of bin `bin` (tile column tx): the bin, plus the
+// following bins of the same tile row while all their records still fit one chunk of `cap`
+// (sparse tiles are sorted together, dense ones alone), never beyond `end`.
+__device__ __forceinline__ uint32_t segment_end(const uint32_t* __restrict__ offsets, int64_t nbins, int64_t bin,
+                                                int tx, int ntx, uint32_t pos, uint32_t end, int cap,
+                                                int group_tiles, int* ntiles) {
+  uint32_t bound[8];                            // ends of this bin and the next 7 (independent loads)
+#pragma unroll
+  for (int k = 0; k < 8; ++k) bound[k] = offsets[min(bin + k + 1, nbins)];
+  uint32_t seg_end = min(end, bound[0]);
+  int nt = 1;
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    if (nt == k && k < group_tiles && tx + k < ntx && seg_end < end) {
+      const uint32_t nxt = min(end, bound[k]);
+      if (nxt - pos <= (uint32_t)cap) {
+        seg_end = nxt;
+        nt = k + 1;
+      }
+    }
+  }
+  *ntiles = nt;
+  return seg_end;
+}
+
+// Work units: unit u covers the estimated-work range [ctotal u / nunits, ctotal (u + 1) /
+// nunits). Cost position x maps to bin b (costoff[b] <= x < costoff[b+1]) and to the record
+// offsets[b] + (x - costoff[b]) / cost_b * count_b, a monotone map, so the units partition
+// the records exactly. CTAs take units from work[0], the last one first; the last CTA to
+// finish leaves work[0] and work[1] zero for the next launch. body(beg, end) runs with the
+// whole CTA.
+template <class Body>
+__device__ __forceinline__ void for_each_unit(const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ costoff,
+                                              int64_t nbins, int nunits, uint32_t* work, Body body) {
+  __shared__ int unit;
+  const uint32_t total = offsets[nbins];
+  const uint32_t ctotal = costoff[nbins];
+  auto split = [&](uint64_t x) -> uint32_t {
+    if (x >= ctotal) return total;
+    const int64_t b = find_bin(costoff, nbins, (uint32_t)x);
+    const uint32_t c0 = costoff[b], cb = costoff[b + 1] - c0;
+    const uint32_t n = offsets[b + 1] - offsets[b];
+    return offsets[b] + (uint32_t)(((uint64_t)(x - c0) * n) / cb);
+  };
+  for (;;) {
+    if (threadIdx.x == 0) unit = nunits - 1 - (int)atomicAdd(&work[0], 1u);
+    __syncthreads();
+    const int u = unit;
+    __syncthreads();
+    if (u < 0) break;
+    const uint32_t beg = split((uint64_t)ctotal * u / nunits);
+    const uint32_t end = split((uint64_t)ctotal * (u + 1) / nunits);
+    if (beg < end) body(beg, end);
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&work[1], 1u) == gridDim.x - 1) {
+      work[0] = 0u;
+      work[1] = 0u;
+      __threadfence();
+    }
+  }
+}
+
+}  // namespace
+}  // namespace wp

@@ -304,7 +304,7 @@ int wp_create(wp_ctx** out, const wp_params* p) {
             dalloc(&ctx->d_partials, (size_t)scan_tiles + 1) == cudaSuccess &&
             dalloc(&ctx->d_costoff, (size_t)ctx->nbins + 1) == cudaSuccess &&
             dalloc(&ctx->d_partials2, (size_t)scan_tiles + 1) == cudaSuccess &&
-            dalloc(&ctx->d_work, 2) == cudaSuccess && cudaMemset(ctx->d_work, 0, 2 * sizeof(uint32_t)) == cudaSuccess &&
+            dalloc(&ctx->d_work, 4) == cudaSuccess && cudaMemset(ctx->d_work, 0, 4 * sizeof(uint32_t)) == cudaSuccess &&
             dalloc(&ctx->d_dropped, 1) == cudaSuccess && dalloc(&ctx->d_wsum, 1) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
