@@ -144,6 +144,18 @@ int wp_grid_noalloc(wp_ctx* ctx, const double* uvw, const double* freq, const vo
 int wp_degrid(wp_ctx* ctx, const double* uvw, const double* freq, const void* grid,
               int64_t nrow, int32_t nchan, void* vis_out, void* stream);
 
+/* Degridding of the visibilities of this context's most recent wp_grid call, reusing that
+ * call's coordinates and binning instead of computing them again (in an imaging loop the same
+ * visibilities are gridded and degridded every cycle). The result is the one wp_degrid gives
+ * for that call's uvw, freq, nrow and nchan, element for element: the Hermitian partners that
+ * wp_grid added are skipped, dropped visibilities get 0.
+ *   grid device [N][N] float2 (read only); vis_out device [nrow][nchan] float2 (overwritten),
+ *   nrow and nchan those of the wp_grid call.
+ * The binning stays valid until the context's next wp_grid, wp_grid_noalloc or wp_degrid.
+ * Errors: WP_ESTATE when there is no such wp_grid call (none yet, or a later wp_degrid or
+ * wp_grid_noalloc replaced its binning); WP_EINVAL, WP_ECUDA. */
+int wp_degrid_last(wp_ctx* ctx, const void* grid, void* vis_out, void* stream);
+
 /* Dirty image from the grid (the IFFT of Fig. 1 / Fig. 2) with the taper correction:
  *   I[j][i] = Re sum_{h,g} G[h][g] exp(+2 pi i ((g-N/2)(i-N/2) + (h-N/2)(j-N/2))/N)
  *             / (sum_w * t(x_i) t(x_j)),  x_i = 2 (i - N/2)/N   (no t factor if !taper_correct)

@@ -17,7 +17,7 @@ _TABLES = {"f32": WP_TABLE_F32, "f16": WP_TABLE_F16, "bf16": WP_TABLE_BF16}
 # every function declared in include/wproj.h
 SYMBOLS = ("wp_create", "wp_destroy", "wp_last_error", "wp_make_wkernels", "wp_grid", "wp_degrid",
            "wp_fft_to_image", "wp_plane_info", "wp_coords", "wp_wkernel_export", "wp_wkernel_norm",
-           "wp_profile", "wp_profile_read", "wp_taper_eval_host", "wp_grid_noalloc")
+           "wp_profile", "wp_profile_read", "wp_taper_eval_host", "wp_grid_noalloc", "wp_degrid_last")
 PHASES = ("wkernels", "plan", "grid", "degrid", "fft", "image")
 
 
@@ -48,6 +48,7 @@ def _load():
     L.wp_make_wkernels.argtypes = [P, P]
     L.wp_grid.argtypes = [P, P, P, P, P, I64, I32, I32, P, P, P, P]
     L.wp_degrid.argtypes = [P, P, P, P, I64, I32, P, P]
+    L.wp_degrid_last.argtypes = [P, P, P, P]
     L.wp_fft_to_image.argtypes = [P, P, P, I32, P, P]
     L.wp_plane_info.argtypes = [P, P, P]
     L.wp_coords.argtypes = [P, P, P, I64, I32, I32, P, P]
@@ -153,8 +154,10 @@ class WProj:
         if n_dropped is None:
             n_dropped = torch.zeros(1, dtype=torch.int64, device=dev)
         flags = (WP_ACCUMULATE if accumulate else 0) | (WP_HERMITIAN_PAIRS if hermitian_pairs else 0)
+        self._last_grid_shape = None
         self._check(lib.wp_grid(self._h, _ptr(uvw), _ptr(freq), _ptr(vis), _ptr(weight), nrow, nchan, flags,
                                 _ptr(grid), _ptr(sum_w), _ptr(n_dropped), self._stream(stream)), "wp_grid")
+        self._last_grid_shape = (nrow, nchan)
         return grid, sum_w, n_dropped
 
     def degrid(self, uvw, freq, grid, vis_out=None, stream=None):
@@ -166,8 +169,22 @@ class WProj:
         if vis_out is None:
             vis_out = torch.empty((nrow, nchan), dtype=torch.complex64, device=grid.device)
         _dev_tensor(vis_out, torch.complex64, "vis_out", (nrow, nchan))
+        self._last_grid_shape = None
         self._check(lib.wp_degrid(self._h, _ptr(uvw), _ptr(freq), _ptr(grid), nrow, nchan, _ptr(vis_out),
                                   self._stream(stream)), "wp_degrid")
+        return vis_out
+
+    def degrid_last(self, grid, vis_out=None, stream=None):
+        """Degrids the visibilities of the most recent grid() call, reusing its binning (wp_degrid_last)."""
+        import torch
+        _dev_tensor(grid, torch.complex64, "grid", (self.n, self.n))
+        shape = getattr(self, "_last_grid_shape", None)
+        if shape is None:
+            raise WProjError(WP_ESTATE, "degrid_last: no grid() binning to reuse")
+        if vis_out is None:
+            vis_out = torch.empty(shape, dtype=torch.complex64, device=grid.device)
+        _dev_tensor(vis_out, torch.complex64, "vis_out", shape)
+        self._check(lib.wp_degrid_last(self._h, _ptr(grid), _ptr(vis_out), self._stream(stream)), "wp_degrid_last")
         return vis_out
 
     def fft_to_image(self, grid, sum_w, taper_correct: bool = True, image=None, stream=None):

@@ -35,6 +35,7 @@ struct D2Args {
   const int64_t* tab_off;
   const float2* grid;
   float2* out;              // visibilities in caller order (record x = caller index)
+  const uint32_t* index;    // gridding plan's visibility index per record (partners flagged), or nullptr
   int smem_bytes;
   int group_tiles;
   int nunits;
@@ -162,8 +163,8 @@ __device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, 
   const int warp = threadIdx.x >> 5;
   for (uint32_t c0 = s0; c0 < s1; c0 += (uint32_t)cap) {
     const int m = (int)min((uint32_t)cap, s1 - c0);
-    sort_chunk<S>((const uint4*)a.recs, c0, m, x0, y0, width, keys, a.g.os, rec_off);
-    const int beg = (int)((int64_t)m * warp / kWarps), end = (int)((int64_t)m * (warp + 1) / kWarps);
+    const int kept = sort_chunk<S>((const uint4*)a.recs, a.index, c0, m, x0, y0, width, keys, a.g.os, rec_off);
+    const int beg = (int)((int64_t)kept * warp / kWarps), end = (int)((int64_t)kept * (warp + 1) / kWarps);
     warp_degrid<S>(tab_off, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
     __syncthreads();
   }
@@ -241,7 +242,8 @@ size_t degrid_v2_smem(const wp_ctx* ctx, int* group_tiles) {
   return bytes;
 }
 
-cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* out, cudaStream_t s, bool* used) {
+cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* out, const uint32_t* index,
+                             cudaStream_t s, bool* used) {
   int group = 1;
   const size_t smem = degrid_v2_smem(ctx, &group);
   *used = smem != 0;
@@ -256,6 +258,7 @@ cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* out, cudaS
   a.tab_off = ctx->d_tab_off;
   a.grid = grid;
   a.out = out;
+  a.index = index;
   a.smem_bytes = (int)smem;
   a.group_tiles = group;
   a.nunits = ctx->nsm * kUnitsPerCta;

@@ -134,7 +134,8 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_degrid_v1(const Record* __restrict__ recs,
                                                         const uint32_t* __restrict__ offsets, int64_t nbins,
                                                         Geometry g, TableRef tr, const float2* __restrict__ grid,
-                                                        float2* __restrict__ out) {
+                                                        float2* __restrict__ out,
+                                                        const uint32_t* __restrict__ index) {
   const uint32_t total = offsets[nbins];
   const uint32_t beg = (uint32_t)((uint64_t)total * blockIdx.x / gridDim.x);
   const uint32_t end = (uint32_t)((uint64_t)total * (blockIdx.x + 1) / gridDim.x);
@@ -151,6 +152,8 @@ __global__ void __launch_bounds__(kThreads) k_degrid_v1(const Record* __restrict
     const T* tab = (const T*)tr.tab + tr.tab_off[p];
     for (uint32_t r = pos + warp; r < seg_end; r += kWarps) {
       const Record rec = recs[r];
+      const uint32_t idx = index ? index[r] : rec.x;
+      if (idx >> 31) continue;                     // a gridding plan's Hermitian partner
       const int i0 = rec.z & 0xffff, j0 = rec.z >> 16;
       const int ox = rec.w & 0xff, oy = (rec.w >> 8) & 0xff;
       // conj(K_k): K_k = K (w >= 0) or conj(K) (w < 0)
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) k_degrid_v1(const Record* __restrict
         sr += __shfl_xor_sync(0xffffffffu, sr, off);
         si += __shfl_xor_sync(0xffffffffu, si, off);
       }
-      if (lane == 0) out[rec.x] = make_float2(sr, si);
+      if (lane == 0) out[idx] = make_float2(sr, si);
     }
     pos = seg_end;
   }
@@ -188,10 +191,10 @@ cudaError_t grid_typed(wp_ctx* ctx, float2* grid, cudaStream_t s) {
 }
 
 template <class T>
-cudaError_t degrid_typed(wp_ctx* ctx, const float2* grid, float2* out, cudaStream_t s) {
+cudaError_t degrid_typed(wp_ctx* ctx, const float2* grid, float2* out, const uint32_t* index, cudaStream_t s) {
   TableRef tr{ctx->d_tab, ctx->d_tab_off};
   k_degrid_v1<T><<<ctx->nsm * 4, kThreads, 0, s>>>((const Record*)ctx->records.ptr, ctx->d_offsets, ctx->nbins,
-                                                   ctx->geo, tr, grid, out);
+                                                   ctx->geo, tr, grid, out, index);
   return cudaGetLastError();
 }
 
@@ -209,15 +212,15 @@ cudaError_t launch_grid(wp_ctx* ctx, float2* grid, cudaStream_t s) {
   }
 }
 
-cudaError_t launch_degrid(wp_ctx* ctx, const float2* grid, float2* out, cudaStream_t s) {
+cudaError_t launch_degrid(wp_ctx* ctx, const float2* grid, float2* out, const uint32_t* index, cudaStream_t s) {
   ++ctx->launches;
   bool used = false;
-  const cudaError_t e = launch_degrid_v2(ctx, grid, out, s, &used);
+  const cudaError_t e = launch_degrid_v2(ctx, grid, out, index, s, &used);
   if (e != cudaSuccess || used) return e;
   switch (ctx->prm.table_type) {
-    case WP_TABLE_F16: return degrid_typed<__half2>(ctx, grid, out, s);
-    case WP_TABLE_BF16: return degrid_typed<__nv_bfloat162>(ctx, grid, out, s);
-    default: return degrid_typed<float2>(ctx, grid, out, s);
+    case WP_TABLE_F16: return degrid_typed<__half2>(ctx, grid, out, index, s);
+    case WP_TABLE_BF16: return degrid_typed<__nv_bfloat162>(ctx, grid, out, index, s);
+    default: return degrid_typed<float2>(ctx, grid, out, index, s);
   }
 }
 

@@ -157,7 +157,7 @@ __device__ __noinline__ void grid_segment(const G2Args& a, int p, bool stage, in
   const int warp = threadIdx.x >> 5;
   for (uint32_t c0 = s0; c0 < s1; c0 += (uint32_t)cap) {
     const int m = (int)min((uint32_t)cap, s1 - c0);
-    sort_chunk<S>((const uint4*)a.recs, c0, m, x0, y0, width, keys, a.g.os, rec_off);
+    sort_chunk<S>((const uint4*)a.recs, nullptr, c0, m, x0, y0, width, keys, a.g.os, rec_off);
     const int beg = (int)((int64_t)m * warp / kWarps), end = (int)((int64_t)m * (warp + 1) / kWarps);
     warp_grid<S>(tab_off, rec_off, beg, end, a.grid, a.g.n);
     __syncthreads();

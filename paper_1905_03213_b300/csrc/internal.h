@@ -104,6 +104,11 @@ struct wp_ctx {
   double* d_chan = nullptr;            // [max_chan][2]: kx_c, kw_c
   int32_t max_chan = 0;
   wp::DeviceBuffer records;
+  wp::DeviceBuffer rounded;            // [3][nvis] int32 rounded coordinates (plan scratch)
+  wp::DeviceBuffer rec_index;          // [records] uint32: visibility index | partner << 31 (wp_grid)
+  bool have_grid_plan = false;         // records/rec_index hold the last wp_grid's binning
+  int64_t plan_nrow = 0;
+  int32_t plan_nchan = 0;
   unsigned long long* d_dropped = nullptr;
   double* d_wsum = nullptr;
 
@@ -136,9 +141,12 @@ cudaError_t launch_coords(wp_ctx* ctx, const double* uvw, int64_t nrow, int32_t 
 cudaError_t launch_grid(wp_ctx* ctx, float2* grid, cudaStream_t s);
 // register-accumulating gridding kernel (grid2.cu); *used = false when the geometry is outside its limits
 cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used);
-cudaError_t launch_degrid(wp_ctx* ctx, const float2* grid, float2* vis_out, cudaStream_t s);
+// index: the gridding plan's visibility indices (degrid that plan's records), or nullptr
+cudaError_t launch_degrid(wp_ctx* ctx, const float2* grid, float2* vis_out, const uint32_t* index,
+                          cudaStream_t s);
 // register-holding degridding kernel (degrid2.cu); *used = false when the geometry is outside its limits
-cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* vis_out, cudaStream_t s, bool* used);
+cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* vis_out, const uint32_t* index,
+                             cudaStream_t s, bool* used);
 // imaging (image.cu)
 cudaError_t launch_image_post(const float2* spectrum, const double* sum_w, const double* taper_img,
                               int32_t taper_correct, float* image, int32_t n, cudaStream_t s);

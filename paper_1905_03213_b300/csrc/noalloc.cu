@@ -95,6 +95,7 @@ extern "C" int wp_grid_noalloc(wp_ctx* ctx, const double* uvw, const double* fre
   if (e != cudaSuccess) return reject(ctx, WP_ECUDA, std::string("wp_grid_noalloc set-up: ") + cudaGetErrorString(e));
 
   cudaStream_t s = (cudaStream_t)stream;
+  ctx->have_grid_plan = false;          // the context's binning is not kept by this call
   ScratchView view(ctx, base);
   const int32_t n = ctx->prm.n;
   if (!(flags & WP_ACCUMULATE)) e = cudaMemsetAsync(grid, 0, sizeof(float2) * (size_t)n * n, s);

@@ -28,24 +28,81 @@ __device__ __forceinline__ int32_t floor_div(int32_t a, int32_t b) {
   return a >= 0 ? a / b : -((-a + b - 1) / b);
 }
 
-// Coordinates of one gridded visibility. (ux, vy, wz) are the float64 products
-// u*kx, v*kx, |w|*kw; `neg` selects the Hermitian partner at -uvw.
-__device__ __forceinline__ Coord make_coord(double ux, double vy, double wz, double w_m, bool neg,
-                                           const Geometry& g) {
+// Round-half-to-even of a float64 with |x| < 2^30 (the caller checks), as an integer, from
+// its bit pattern with integer operations only: x = m 2^(e - 1075) with the 53-bit
+// significand m, so the integer part is m >> (1075 - e) and the dropped bits decide the
+// rounding (above half: up; exactly half: up when the integer part is odd).
+__device__ __forceinline__ int32_t rint_small(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const int sh = 1075 - e;                             // >= 23 for |x| < 2^30
+  if (sh > 53) return 0;                               // |x| < 1/2
+  const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;
+  const unsigned long long q = m >> sh;
+  const unsigned long long rem = m & ((1ull << sh) - 1ull);
+  const unsigned long long half = 1ull << (sh - 1);
+  const int32_t n = (int32_t)q + ((rem > half || (rem == half && (q & 1ull))) ? 1 : 0);
+  return (b >> 63) ? -n : n;
+}
+
+// |x| as float64 bits (sign cleared); finite values compare below 0x7ff0000000000000.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+constexpr unsigned long long kBitsCoordLimit = 0x41D0000000000000ull;   // 2^30
+constexpr unsigned long long kBitsInf = 0x7ff0000000000000ull;
+
+// The rounded coordinates of one visibility, shared by it and its Hermitian partner:
+// U = rint(u kx), V = rint(v kx), plane = min(Nw - 1, rint(min(|w| kw, 2^30))), valid when
+// all three products are finite and |u kx|, |v kx| < 2^30.
+struct Rounded {
+  int32_t u, v, plane;
+  bool fin, wpos, wneg;
+};
+
+// Scratch form of Rounded: u, v and plane | fin << 16 | wpos << 17 | wneg << 18, stored as
+// three arrays of nvis int32.
+__device__ __forceinline__ void store_rounded(int32_t* __restrict__ out, int64_t nvis, int64_t k, const Rounded& r) {
+  out[k] = r.u;
+  out[nvis + k] = r.v;
+  out[2 * nvis + k] = r.plane | (r.fin ? 1 << 16 : 0) | (r.wpos ? 1 << 17 : 0) | (r.wneg ? 1 << 18 : 0);
+}
+__device__ __forceinline__ Rounded load_rounded(const int32_t* __restrict__ in, int64_t nvis, int64_t k) {
+  Rounded r;
+  r.u = in[k];
+  r.v = in[nvis + k];
+  const int32_t f = in[2 * nvis + k];
+  r.plane = f & 0xffff;
+  r.fin = (f >> 16) & 1;
+  r.wpos = (f >> 17) & 1;
+  r.wneg = (f >> 18) & 1;
+  return r;
+}
+
+__device__ __forceinline__ Rounded round_coords(double ux, double vy, double wz, double w_m, const Geometry& g) {
+  Rounded r;
+  const unsigned long long bx = abs_bits(ux), by = abs_bits(vy), bz = abs_bits(wz);
+  r.fin = bx < kBitsCoordLimit && by < kBitsCoordLimit && bz < kBitsInf;
+  r.u = r.fin ? rint_small(ux) : 0;
+  r.v = r.fin ? rint_small(vy) : 0;
+  r.plane = !r.fin ? 0 : (bz >= kBitsCoordLimit ? g.n_w - 1 : min(g.n_w - 1, rint_small(wz)));
+  const unsigned long long bw = (unsigned long long)__double_as_longlong(w_m);
+  r.wpos = (bw >> 63) == 0 && (bw << 1) != 0;        // w > 0
+  r.wneg = (bw >> 63) != 0 && (bw << 1) != 0;        // w < 0
+  return r;
+}
+
+// Coordinates of one gridded visibility from its rounded coordinates; `neg` selects the
+// Hermitian partner at -uvw.
+__device__ __forceinline__ Coord make_coord(const Rounded& r, bool neg, const Geometry& g) {
   Coord c;
-  const bool fin = isfinite(ux) && isfinite(vy) && isfinite(wz) && fabs(ux) < kCoordLimit &&
-                   fabs(vy) < kCoordLimit;
-  int32_t u = fin ? (int32_t)rint(ux) : 0;
-  int32_t v = fin ? (int32_t)rint(vy) : 0;
-  const int32_t p = fin ? (int32_t)fmin((double)(g.n_w - 1), rint(fmin(wz, kCoordLimit))) : 0;
-  if (neg) {
-    u = -u;
-    v = -v;
-  }
+  const int32_t u = neg ? -r.u : r.u;
+  const int32_t v = neg ? -r.v : r.v;
+  const int32_t p = r.plane;
   c.u = u;
   c.v = v;
   c.plane = p;
-  c.conj = neg ? (w_m > 0.0) : (w_m < 0.0);
+  c.conj = neg ? r.wpos : r.wneg;
   const int32_t s = g.supp[p];
   const int32_t half = s * g.os / 2;
   const int32_t x = u + (g.n / 2) * g.os;
@@ -54,7 +111,7 @@ __device__ __forceinline__ Coord make_coord(double ux, double vy, double wz, dou
   c.j0 = floor_div(y - half, g.os) + 1;
   c.ox = c.i0 * g.os - x + half - 1;
   c.oy = c.j0 * g.os - y + half - 1;
-  c.keep = fin && c.i0 >= 0 && c.i0 + s <= g.n && c.j0 >= 0 && c.j0 + s <= g.n;
+  c.keep = r.fin && c.i0 >= 0 && c.i0 + s <= g.n && c.j0 >= 0 && c.j0 + s <= g.n;
   return c;
 }
 
@@ -69,14 +126,14 @@ struct Products {
 
 __device__ __forceinline__ Products products(const double* __restrict__ uvw, const double* __restrict__ chan,
                                              int64_t k, int32_t nchan) {
-  const int64_t r = k / nchan;
-  const int32_t ch = (int32_t)(k - r * nchan);
-  const double u = uvw[3 * r], v = uvw[3 * r + 1], w = uvw[3 * r + 2];
+  const uint32_t r = (uint32_t)k / (uint32_t)nchan;    // nvis < 2^32 (32-bit record offsets)
+  const int32_t ch = (int32_t)((uint32_t)k - r * (uint32_t)nchan);
+  const double u = uvw[3 * (size_t)r], v = uvw[3 * (size_t)r + 1], w = uvw[3 * (size_t)r + 2];
   const double kx = chan[2 * ch], kw = chan[2 * ch + 1];
   Products p;
   p.ux = __dmul_rn(u, kx);
   p.vy = __dmul_rn(v, kx);
-  p.wz = __dmul_rn(fabs(w), kw);
+  p.wz = __dmul_rn(__longlong_as_double(__double_as_longlong(w) & 0x7fffffffffffffffll), kw);
   p.w = w;
   return p;
 }
@@ -105,24 +162,28 @@ __global__ void k_channel_factors(const double* __restrict__ freq, int32_t nchan
   }
 }
 
-// Pass 1: bin histogram, dropped count and kept-weight sum.
+// Pass 1: bin histogram, dropped count and kept-weight sum; optionally the rounded
+// coordinates of every visibility for pass 3.
 __global__ void __launch_bounds__(256) k_histogram(const double* __restrict__ uvw, const double* __restrict__ chan,
                                                    const float* __restrict__ weight, int64_t nvis, int32_t nchan,
                                                    int32_t pairs, Geometry g, uint32_t* __restrict__ counts,
                                                    unsigned long long* __restrict__ dropped,
-                                                   double* __restrict__ wsum) {
+                                                   double* __restrict__ wsum, int32_t* __restrict__ rounded) {
   double my_w = 0.0;
   unsigned long long my_drop = 0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nvis; k += (int64_t)gridDim.x * blockDim.x) {
     const Products pr = products(uvw, chan, k, nchan);
-    const double wt = weight ? (double)weight[k] : 1.0;
+    const Rounded rd = round_coords(pr.ux, pr.vy, pr.wz, pr.w, g);
+    if (rounded) store_rounded(rounded, nvis, k, rd);
+    int nkept = 0;
     for (int h = 0; h <= pairs; ++h) {
-      const Coord c = make_coord(pr.ux, pr.vy, pr.wz, pr.w, h == 1, g);
+      const Coord c = make_coord(rd, h == 1, g);
       const uint32_t key = c.keep ? bin_of(c, g) : 0xffffffffu;
       aggregated_increment(counts, key);
-      if (c.keep) my_w += wt;
-      else ++my_drop;
+      nkept += c.keep ? 1 : 0;
     }
+    my_drop += (unsigned long long)(pairs + 1 - nkept);
+    if (nkept) my_w = fma((double)(weight ? weight[k] : 1.0f), (double)nkept, my_w);
   }
   // block reduction of the two scalars
   __shared__ double sw[8];
@@ -149,14 +210,21 @@ __global__ void __launch_bounds__(256) k_histogram(const double* __restrict__ uv
   }
 }
 
-// Pass 3: scatter records into their bins.
+// Pass 3: scatter records into their bins (coordinates from pass 1's scratch when given).
 __global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ uvw, const double* __restrict__ chan,
                                                  const float2* __restrict__ vis, const float* __restrict__ weight,
                                                  int64_t nvis, int32_t nchan, int32_t pairs, int32_t for_degrid,
                                                  Geometry g, uint32_t* __restrict__ cursor,
-                                                 Record* __restrict__ records) {
+                                                 Record* __restrict__ records, const int32_t* __restrict__ rounded,
+                                                 uint32_t* __restrict__ index) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nvis; k += (int64_t)gridDim.x * blockDim.x) {
-    const Products pr = products(uvw, chan, k, nchan);
+    Rounded rd;
+    if (rounded) {
+      rd = load_rounded(rounded, nvis, k);
+    } else {
+      const Products pr = products(uvw, chan, k, nchan);
+      rd = round_coords(pr.ux, pr.vy, pr.wz, pr.w, g);
+    }
     float2 val = make_float2(0.f, 0.f);
     if (!for_degrid) {
       const float2 v = vis[k];
@@ -164,7 +232,7 @@ __global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ uvw,
       val = make_float2(wt * v.x, wt * v.y);
     }
     for (int h = 0; h <= pairs; ++h) {
-      const Coord c = make_coord(pr.ux, pr.vy, pr.wz, pr.w, h == 1, g);
+      const Coord c = make_coord(rd, h == 1, g);
       const uint32_t key = c.keep ? bin_of(c, g) : 0xffffffffu;
       const uint32_t slot = aggregated_increment(cursor, key);
       if (c.keep) {
@@ -179,6 +247,7 @@ __global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ uvw,
         rec.z = (uint32_t)c.i0 | ((uint32_t)c.j0 << 16);
         rec.w = (uint32_t)c.ox | ((uint32_t)c.oy << 8) | (c.conj ? 0x80000000u : 0u);
         records[slot] = rec;
+        if (index) index[slot] = (uint32_t)k | (h ? 0x80000000u : 0u);
       }
     }
   }
@@ -282,8 +351,9 @@ __global__ void k_coords_out(const double* __restrict__ uvw, const double* __res
                              int32_t nchan, int32_t pairs, Geometry g, int32_t* __restrict__ out) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nvis; k += (int64_t)gridDim.x * blockDim.x) {
     const Products pr = products(uvw, chan, k, nchan);
+    const Rounded rd = round_coords(pr.ux, pr.vy, pr.wz, pr.w, g);
     for (int h = 0; h <= pairs; ++h) {
-      const Coord c = make_coord(pr.ux, pr.vy, pr.wz, pr.w, h == 1, g);
+      const Coord c = make_coord(rd, h == 1, g);
       int32_t* o = out + 8 * (k + h * nvis);
       o[0] = c.u;
       o[1] = c.v;
@@ -319,10 +389,15 @@ cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const
   if ((e = cudaMemsetAsync(ctx->d_dropped, 0, sizeof(unsigned long long), s))) return e;
   if ((e = cudaMemsetAsync(ctx->d_wsum, 0, sizeof(double), s))) return e;
   const int blocks = grid_blocks(nvis, ctx->nsm);
+  // pass 1 keeps the rounded coordinates for pass 3 when the context's scratch holds them
+  int32_t* rounded = ctx->rounded.bytes >= (size_t)nvis * 12 ? (int32_t*)ctx->rounded.ptr : nullptr;
+  // a gridding plan also records each record's visibility index, for wp_degrid_last
+  const size_t nrec = (size_t)nvis * (pairs ? 2 : 1);
+  uint32_t* index = (!for_degrid && ctx->rec_index.bytes >= nrec * 4) ? (uint32_t*)ctx->rec_index.ptr : nullptr;
   ctx->launches += 3 + (nvis > 0 ? 2 : 0);  // prefix sum (3), histogram and scatter
   if (nvis > 0) {
     k_histogram<<<blocks, 256, 0, s>>>(uvw, ctx->d_chan, for_degrid ? nullptr : weight, nvis, nchan, pairs ? 1 : 0,
-                                       ctx->geo, ctx->d_counts, ctx->d_dropped, ctx->d_wsum);
+                                       ctx->geo, ctx->d_counts, ctx->d_dropped, ctx->d_wsum, rounded);
     if ((e = cudaGetLastError())) return e;
   }
   const int64_t tiles = (ctx->nbins + kScanTile - 1) / kScanTile;
@@ -335,7 +410,7 @@ cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const
   if ((e = cudaGetLastError())) return e;
   if (nvis > 0) {
     k_scatter<<<blocks, 256, 0, s>>>(uvw, ctx->d_chan, vis, weight, nvis, nchan, pairs ? 1 : 0, for_degrid ? 1 : 0,
-                                     ctx->geo, ctx->d_cursor, (Record*)ctx->records.ptr);
+                                     ctx->geo, ctx->d_cursor, (Record*)ctx->records.ptr, rounded, index);
     if ((e = cudaGetLastError())) return e;
   }
   return cudaSuccess;

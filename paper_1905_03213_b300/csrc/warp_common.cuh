@@ -176,43 +176,55 @@ __device__ __forceinline__ void stage_table(const float2* __restrict__ src, int 
 // tile row, columns x0 .. x0 + width, rows y0 .. y0 + tile_y) by origin key (row-major within
 // the segment) into the shared array at byte offset rec_off, decoding each into
 //   x, y : as binned;  z : i0 | j0 << 16;  w : class byte offset in the staged table | conj << 31.
-// On return counts[key] (the shared counters at offset 0) is the end of the key's records.
+// With `index` (a gridding plan's visibility index per record, partner flag in bit 31) the
+// Hermitian partners are left out and x becomes the visibility index. Returns the number of
+// records sorted; counts[key] (the shared counters at offset 0) is then the end of each key.
 template <int S>
-__device__ __forceinline__ void sort_chunk(const uint4* __restrict__ grecs, uint32_t c0, int m, int x0, int y0,
-                                           int width, int keys, int os, int rec_off) {
+__device__ __forceinline__ int sort_chunk(const uint4* __restrict__ grecs, const uint32_t* __restrict__ index,
+                                          uint32_t c0, int m, int x0, int y0, int width, int keys, int os,
+                                          int rec_off) {
   using L = Lay<S>;
   uint32_t* counts = (uint32_t*)dyn_smem();
   uint4* drec = (uint4*)(dyn_smem() + rec_off);
-  for (int k = threadIdx.x; k < keys; k += kThreads) counts[k] = 0u;
+  for (int k = threadIdx.x; k <= keys; k += kThreads) counts[k] = 0u;
   __syncthreads();
   // pass 1: histogram of the origin keys, 4 loads in flight
   for (int r0 = threadIdx.x; r0 < m; r0 += 4 * kThreads) {
     uint32_t z[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) z[u] = r0 + u * kThreads < m ? __ldcg(&grecs[c0 + r0 + u * kThreads].z) : kNoOrigin;
+    for (int u = 0; u < 4; ++u) {
+      const int r = r0 + u * kThreads;
+      z[u] = (r < m && !(index && (index[c0 + r] >> 31))) ? __ldcg(&grecs[c0 + r].z) : kNoOrigin;
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
       if (z[u] != kNoOrigin) atomicAdd(&counts[((int)(z[u] >> 16) - y0) * width + ((int)(z[u] & 0xffff) - x0)], 1u);
   }
   __syncthreads();
-  block_exclusive_scan(keys);
+  block_exclusive_scan(keys + 1);
+  const int kept = (int)counts[keys];
   // pass 2: decode each record into its sorted slot
   for (int r0 = threadIdx.x; r0 < m; r0 += 4 * kThreads) {
     uint4 rec[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (r0 + u * kThreads < m) rec[u] = __ldcs(grecs + c0 + r0 + u * kThreads);
+    uint32_t idx[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      if (r0 + u * kThreads < m) {
+      const int r = r0 + u * kThreads;
+      idx[u] = (r < m && index) ? index[c0 + r] : 0u;
+      if (r < m) rec[u] = __ldcs(grecs + c0 + r);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (r0 + u * kThreads < m && !(idx[u] >> 31)) {
         const int key = ((int)(rec[u].z >> 16) - y0) * width + ((int)(rec[u].z & 0xffff) - x0);
         const int cls = (int)((rec[u].w >> 8) & 0xff) * os + (int)(rec[u].w & 0xff);
         const uint32_t w = (uint32_t)(cls * L::CB) | (rec[u].w & 0x80000000u);
-        drec[atomicAdd(&counts[key], 1u)] = make_uint4(rec[u].x, rec[u].y, rec[u].z, w);
+        drec[atomicAdd(&counts[key], 1u)] = make_uint4(index ? idx[u] : rec[u].x, rec[u].y, rec[u].z, w);
       }
     }
   }
   __syncthreads();
+  return kept;
 }
 
 // The segment starting at record `pos` of bin `bin` (tile column tx): the bin, plus the

@@ -125,7 +125,7 @@ __global__ void k_store_scalars(const double* wsum, const unsigned long long* dr
 }
 
 int prepare_vis_call(wp_ctx* ctx, const double* uvw, const double* freq, int64_t nrow, int32_t nchan, int pairs,
-                     cudaStream_t s) {
+                     bool want_index, cudaStream_t s) {
   int rc = check_vis_args(ctx, uvw, freq, nrow, nchan, pairs);
   if (rc) return rc;
   if (!ctx->have_kernels) return fail(ctx, WP_ESTATE, "wp_make_wkernels has not been called");
@@ -133,6 +133,9 @@ int prepare_vis_call(wp_ctx* ctx, const double* uvw, const double* freq, int64_t
   if ((rc = ensure_channels(ctx, nchan))) return rc;
   const size_t ng = (size_t)nrow * nchan * (pairs ? 2 : 1);
   if ((rc = ensure_buffer(ctx, ctx->records, std::max<size_t>(ng, 1) * sizeof(wp::Record), "records"))) return rc;
+  if ((rc = ensure_buffer(ctx, ctx->rounded, std::max<size_t>((size_t)nrow * nchan, 1) * 12, "coordinate scratch"))) return rc;
+  if (want_index && (rc = ensure_buffer(ctx, ctx->rec_index, std::max<size_t>(ng, 1) * 4, "record indices"))) return rc;
+  ctx->have_grid_plan = false;          // the records are about to be replaced
   if (nrow > 0) {
     WP_CUDA(ctx, wp::launch_channel_factors(freq, nchan, ctx->geo.os_l, ctx->geo.wscale, ctx->d_chan, s));
     ++ctx->launches;
@@ -186,7 +189,7 @@ void wp_destroy(wp_ctx* ctx) {
                   ctx->d_stage,    ctx->d_quad,      ctx->d_tab64,     ctx->d_tab,      ctx->d_supp,
                   ctx->d_wplane,   ctx->d_tab_off,   ctx->d_tab64_off, ctx->d_quad_off, ctx->d_nu,
                   ctx->d_counts,   ctx->d_offsets,   ctx->d_cursor,    ctx->d_partials, ctx->d_chan,
-                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2, ctx->d_work};
+                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2, ctx->d_work, ctx->rounded.ptr, ctx->rec_index.ptr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -348,7 +351,7 @@ int wp_grid(wp_ctx* ctx, const double* uvw, const double* freq, const void* vis,
   if (nrow > 0 && !vis) return fail(ctx, WP_EINVAL, "vis must not be NULL");
   const int pairs = (flags & WP_HERMITIAN_PAIRS) ? 1 : 0;
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = prepare_vis_call(ctx, uvw, freq, nrow, nchan, pairs, s);
+  int rc = prepare_vis_call(ctx, uvw, freq, nrow, nchan, pairs, true, s);
   if (rc) return rc;
   const int32_t n = ctx->prm.n;
   if (!(flags & WP_ACCUMULATE)) WP_CUDA(ctx, cudaMemsetAsync(grid, 0, sizeof(float2) * (size_t)n * n, s));
@@ -356,6 +359,9 @@ int wp_grid(wp_ctx* ctx, const double* uvw, const double* freq, const void* vis,
     Phase ph(ctx, WP_PHASE_PLAN, s);
     WP_CUDA(ctx, wp::launch_plan(ctx, uvw, (const float2*)vis, weight, nrow, nchan, pairs != 0, false, s));
   }
+  ctx->have_grid_plan = true;
+  ctx->plan_nrow = nrow;
+  ctx->plan_nchan = nchan;
   {
     Phase ph(ctx, WP_PHASE_GRID, s);
     WP_CUDA(ctx, wp::launch_grid(ctx, (float2*)grid, s));
@@ -375,7 +381,7 @@ int wp_degrid(wp_ctx* ctx, const double* uvw, const double* freq, const void* gr
   if (!grid) return fail(ctx, WP_EINVAL, "grid must not be NULL");
   if (nrow > 0 && !vis_out) return fail(ctx, WP_EINVAL, "vis_out must not be NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = prepare_vis_call(ctx, uvw, freq, nrow, nchan, 0, s);
+  int rc = prepare_vis_call(ctx, uvw, freq, nrow, nchan, 0, false, s);
   if (rc) return rc;
   if (nrow == 0) return WP_OK;
   WP_CUDA(ctx, cudaMemsetAsync(vis_out, 0, sizeof(float2) * (size_t)nrow * nchan, s));
@@ -385,7 +391,24 @@ int wp_degrid(wp_ctx* ctx, const double* uvw, const double* freq, const void* gr
   }
   {
     Phase ph(ctx, WP_PHASE_DEGRID, s);
-    WP_CUDA(ctx, wp::launch_degrid(ctx, (const float2*)grid, (float2*)vis_out, s));
+    WP_CUDA(ctx, wp::launch_degrid(ctx, (const float2*)grid, (float2*)vis_out, nullptr, s));
+  }
+  return WP_OK;
+}
+
+int wp_degrid_last(wp_ctx* ctx, const void* grid, void* vis_out, void* stream) {
+  if (!ctx) return WP_EINVAL;
+  if (!ctx->have_grid_plan) return fail(ctx, WP_ESTATE, "no wp_grid binning to reuse (none yet, or replaced since)");
+  if (!grid) return fail(ctx, WP_EINVAL, "grid must not be NULL");
+  const int64_t nvis = ctx->plan_nrow * ctx->plan_nchan;
+  if (nvis > 0 && !vis_out) return fail(ctx, WP_EINVAL, "vis_out must not be NULL");
+  if (nvis == 0) return WP_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  WP_CUDA(ctx, cudaSetDevice(ctx->prm.device));
+  WP_CUDA(ctx, cudaMemsetAsync(vis_out, 0, sizeof(float2) * (size_t)nvis, s));
+  {
+    Phase ph(ctx, WP_PHASE_DEGRID, s);
+    WP_CUDA(ctx, wp::launch_degrid(ctx, (const float2*)grid, (float2*)vis_out, (const uint32_t*)ctx->rec_index.ptr, s));
   }
   return WP_OK;
 }

@@ -228,6 +228,33 @@ def test_degrid_parity(torch_cuda, which):
     np.testing.assert_array_equal(out.ravel()[~crd["keep"]], 0)
 
 
+@pytest.mark.parametrize("pairs,table", [(False, "f32"), (True, "f32"), (True, "f16")])
+def test_degrid_last_reuses_grid_binning(torch_cuda, pairs, table):
+    """wp_degrid_last after wp_grid equals wp_degrid on the same visibilities, element for
+    element (the partners wp_grid added are skipped, dropped visibilities are 0), and against
+    the oracle within the degridding tolerance."""
+    import torch
+    import paper_1905_03213_b300 as W
+    case = random_case(n=128, nrow=1500, nchan=3, s_min=5, s_max=12, pairs=pairs, off_grid=0.1)
+    wp = make_wproj(case, table=table)
+    uvw, f, vis, wt = to_dev(case)
+    G = torch.from_numpy(synth.random_grid(case.prm.n, 21)).cuda()
+    wp.grid(uvw, f, vis, wt, hermitian_pairs=pairs)
+    last = wp.degrid_last(G)
+    own = wp.degrid(uvw, f, G)
+    assert torch.equal(last, own)
+    crd = oracle.coords(case.uvw, case.freqs, case.prm)
+    assert (~crd["keep"]).sum() > 0
+    np.testing.assert_array_equal(last.cpu().numpy().ravel()[~crd["keep"]], 0)
+    if table == "f32":
+        ref = oracle.degrid(crd, G.cpu().numpy().astype(np.complex128), case.tables, case.prm).reshape(case.vis.shape)
+        e, _ = peak_rel(last.cpu().numpy(), ref)
+        assert e < 1e-5, e
+    # wp_degrid replaced the binning: a second degrid_last is refused
+    rc = W.lib.wp_degrid_last(wp._h, G.data_ptr(), last.data_ptr(), None)
+    assert rc == W.WP_ESTATE
+
+
 def test_adjoint_dot_product_gpu(torch_cuda):
     """<grid(c), G> = <c, degrid(G)> with unit weights, both on the GPU (float32)."""
     import torch
@@ -258,3 +285,9 @@ def test_profile_counts_phases_and_launches(torch_cuda):
     # 6 kernel-table + (1 channel + 5 plan + 4 work-estimate scan + 1 grid + 1 scalars)
     # + (1 channel + 5 plan + 4 work-estimate scan + 1 degrid) + 1 image
     assert launches == 30
+    # degridding the gridded visibilities again reuses wp_grid's binning: no plan phase
+    g, sw, _ = wp.grid(uvw, f, vis, wt)
+    wp.profile_read()
+    wp.degrid_last(g)
+    ms, cnt, launches = wp.profile_read()
+    assert {k: v for k, v in cnt.items() if v} == {"degrid": 1} and launches == 5
