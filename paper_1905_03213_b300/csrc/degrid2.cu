@@ -31,7 +31,7 @@ struct D2Args {
   const uint32_t* costoff;  // [nbins + 1] prefix sums of per-bin work estimates
   int64_t nbins;
   Geometry g;
-  const float2* tab;        // stored tables (f32), layout [plane][oy*os+ox][a][b]
+  const void* tab;          // stored tables (f32, f16 or bf16 taps), layout [plane][oy*os+ox][a][b]
   const int64_t* tab_off;
   const float2* grid;
   float2* out;              // visibilities in caller order (record x = caller index)
@@ -75,7 +75,7 @@ __device__ __forceinline__ void batch_reduce(float (&v)[NB], int lane) {
 
 // One warp degrids the decoded, sorted records [beg, end) of the chunk at byte offset rec_off
 // from the grid region staged at sub_off (pitch entries per row, origin (sx0, sy0)).
-template <int S>
+template <int S, class T>
 __device__ __forceinline__ void warp_degrid(int tab_off, int sub_off, int pitch, int sx0, int sy0, int rec_off,
                                             int beg, int end, float2* __restrict__ out) {
   using L = Lay<S>;
@@ -98,7 +98,7 @@ __device__ __forceinline__ void warp_degrid(int tab_off, int sub_off, int pitch,
       pre[r] = pim[r] = 0.f;
       if (b0 + r < end) {                          // warp-uniform
         const uint4 rec = drec[b0 + r];
-        Taps<S> tv;
+        Taps<S, T> tv;
         tv.load(tab + (rec.w & 0x7fffffffu), lane);
         if (rec.z != cz) {                         // warp-uniform: load the cells under the new origin
           cz = rec.z;
@@ -122,8 +122,8 @@ __device__ __forceinline__ void warp_degrid(int tab_off, int sub_off, int pitch,
         unsigned long long PR = 0ull, PI = 0ull;
 #pragma unroll
         for (int k = 0; k < L::RP; ++k) {
-          const unsigned long long kr = pack2(tv.r[k].x, tv.r[k].y);
-          const unsigned long long ki = fma2(pack2(tv.i[k].x, tv.i[k].y), SG, 0ull);
+          const unsigned long long kr = tv.r[k];
+          const unsigned long long ki = fma2(tv.i[k], SG, 0ull);
           PR = fma2(kr, GR[k], PR);                // re: gr kr - gi ki'
           PR = fma2(ki, NGI[k], PR);
           PI = fma2(ki, GR[k], PI);                // im: gr ki' + gi kr
@@ -131,9 +131,9 @@ __device__ __forceinline__ void warp_degrid(int tab_off, int sub_off, int pitch,
         }
         float sr = lo_of(PR) + hi_of(PR), si = lo_of(PI) + hi_of(PI);
         if (L::RT) {
-          const float kt = sg * tv.t.y;
-          sr = fmaf(gtr, tv.t.x, fmaf(-gti, kt, sr));
-          si = fmaf(gtr, kt, fmaf(gti, tv.t.x, si));
+          const float kt = sg * tv.ti;
+          sr = fmaf(gtr, tv.tr, fmaf(-gti, kt, sr));
+          si = fmaf(gtr, kt, fmaf(gti, tv.tr, si));
         }
         pre[r] = sr;
         pim[r] = si;
@@ -145,12 +145,12 @@ __device__ __forceinline__ void warp_degrid(int tab_off, int sub_off, int pitch,
   }
 }
 
-template <int S>
+template <int S, class T>
 __device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, int x0, int y0, int width,
                                             uint32_t s0, uint32_t s1, int cap, int tab_off, int sub_off,
                                             int rec_off) {
   using L = Lay<S>;
-  if (stage) stage_table<S>(a.tab + a.tab_off[p], a.g.os, tab_off);
+  if (stage) stage_table<S, T>((const T*)a.tab + a.tab_off[p], a.g.os, tab_off);
   // the grid region under the segment's footprints (cells outside the grid read as zero)
   const int cols = width + S - 1, rows = sub_rows(a.g.tile_y, S), pitch = sub_pitch(cols);
   float2* sub = (float2*)(dyn_smem() + sub_off);
@@ -163,14 +163,15 @@ __device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, 
   const int warp = threadIdx.x >> 5;
   for (uint32_t c0 = s0; c0 < s1; c0 += (uint32_t)cap) {
     const int m = (int)min((uint32_t)cap, s1 - c0);
-    const int kept = sort_chunk<S>((const uint4*)a.recs, a.index, c0, m, x0, y0, width, keys, a.g.os, rec_off);
+    const int kept = sort_chunk<S, T>((const uint4*)a.recs, a.index, c0, m, x0, y0, width, keys, a.g.os, rec_off);
     const int beg = (int)((int64_t)kept * warp / kWarps), end = (int)((int64_t)kept * (warp + 1) / kWarps);
-    warp_degrid<S>(tab_off, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
+    warp_degrid<S, T>(tab_off, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
     __syncthreads();
   }
   (void)L::R;
 }
 
+template <class T>
 __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
   int64_t bin = find_bin(a.offsets, a.nbins, beg);
   uint32_t pos = beg;
@@ -182,7 +183,7 @@ __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
     const int64_t tile = bin - (int64_t)p * a.g.ntiles;
     const int ty = (int)(tile / a.g.ntx), tx = (int)(tile - (int64_t)ty * a.g.ntx);
     const int s = a.g.supp[p];
-    const int sub_off = tab_off + a.g.os * a.g.os * lay_class_bytes(s);
+    const int sub_off = tab_off + a.g.os * a.g.os * lay_class_bytes(s, TabElem<T>::E);
     const int rec_off = sub_off + sub_bytes(a.g.tile_x, a.g.tile_y, a.group_tiles, s);
     const int cap = (a.smem_bytes - rec_off) / (int)sizeof(Record);
     int ntiles = 1;
@@ -194,7 +195,7 @@ __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
     switch (s) {
 #define WP_SEG_CASE(N)                                                                                   \
   case N:                                                                                                \
-    degrid_segment<N>(a, p, stage, x0, y0, width, pos, seg_end, cap, tab_off, sub_off, rec_off);         \
+    degrid_segment<N, T>(a, p, stage, x0, y0, width, pos, seg_end, cap, tab_off, sub_off, rec_off);         \
     break;
       WP_SEG_CASE(1) WP_SEG_CASE(2) WP_SEG_CASE(3) WP_SEG_CASE(4) WP_SEG_CASE(5) WP_SEG_CASE(6) WP_SEG_CASE(7)
       WP_SEG_CASE(8) WP_SEG_CASE(9) WP_SEG_CASE(10) WP_SEG_CASE(11) WP_SEG_CASE(12) WP_SEG_CASE(13)
@@ -207,9 +208,10 @@ __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
   }
 }
 
+template <class T>
 __global__ void __launch_bounds__(kThreads, 1) k_degrid_v2(D2Args a) {
   for_each_unit(a.offsets, a.costoff, a.nbins, a.nunits, a.work,
-                [&](uint32_t beg, uint32_t end) { degrid_range(a, beg, end); });
+                [&](uint32_t beg, uint32_t end) { degrid_range<T>(a, beg, end); });
 }
 
 }  // namespace
@@ -218,7 +220,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_degrid_v2(D2Args a) {
 // (then the baseline kernel of grid.cu runs).
 size_t degrid_v2_smem(const wp_ctx* ctx, int* group_tiles) {
   const int smax = *std::max_element(ctx->supp.begin(), ctx->supp.end());
-  if (smax > kMaxS || ctx->prm.table_type != WP_TABLE_F32) return 0;
+  if (smax > kMaxS) return 0;
+  const int e = ctx->prm.table_type == WP_TABLE_F32 ? 4 : 2;
   const int os = ctx->prm.oversample;
   const int tx = ctx->geo.tile_x, ty = ctx->geo.tile_y;
   if ((int64_t)tx * ty > kMaxKeys) return 0;
@@ -231,7 +234,7 @@ size_t degrid_v2_smem(const wp_ctx* ctx, int* group_tiles) {
   for (; group >= 1; --group) {
     bool fits = true;
     for (int sp : ctx->supp) {
-      const size_t need = (size_t)kCountsBytes + (size_t)os * os * lay_class_bytes(sp) +
+      const size_t need = (size_t)kCountsBytes + (size_t)os * os * lay_class_bytes(sp, e) +
                           (size_t)sub_bytes(tx, ty, group, sp) + (size_t)kMinChunk * sizeof(Record);
       if (need > bytes) fits = false;
     }
@@ -254,7 +257,7 @@ cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* out, const
   a.costoff = ctx->d_costoff;
   a.nbins = ctx->nbins;
   a.g = ctx->geo;
-  a.tab = (const float2*)ctx->d_tab;
+  a.tab = ctx->d_tab;
   a.tab_off = ctx->d_tab_off;
   a.grid = grid;
   a.out = out;
@@ -265,9 +268,17 @@ cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* out, const
   a.work = ctx->d_work + 2;
   cudaError_t e;
   if ((e = launch_bin_costs(ctx, s))) return e;
-  if ((e = cudaFuncSetAttribute(k_degrid_v2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-  k_degrid_v2<<<ctx->nsm, kThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  auto run = [&](auto kern) -> cudaError_t {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err) return err;
+    kern<<<ctx->nsm, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+  };
+  switch (ctx->prm.table_type) {
+    case WP_TABLE_F16: return run(k_degrid_v2<__half2>);
+    case WP_TABLE_BF16: return run(k_degrid_v2<__nv_bfloat162>);
+    default: return run(k_degrid_v2<float2>);
+  }
 }
 
 }  // namespace wp

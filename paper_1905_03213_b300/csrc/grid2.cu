@@ -38,7 +38,7 @@ struct G2Args {
   const uint32_t* costoff;  // [nbins + 1] prefix sums of per-bin work estimates
   int64_t nbins;
   Geometry g;
-  const float2* tab;        // stored tables (f32), layout [plane][oy*os+ox][a][b]
+  const void* tab;          // stored tables (f32, f16 or bf16 taps), layout [plane][oy*os+ox][a][b]
   const int64_t* tab_off;
   float2* grid;
   int smem_bytes;           // dynamic shared memory of the launch
@@ -65,10 +65,10 @@ struct Footprint {
     float2* p = grid + (int64_t)(j0 + row0) * n + col0 + a;
 #pragma unroll
     for (int k = 0; k < L::RP; ++k) {
-      if (row0 + 2 * k < S) atomicAdd(p + (int64_t)(2 * k) * n, make_float2(lo_of(re[k]), lo_of(im[k])));
-      if (row0 + 2 * k + 1 < S) atomicAdd(p + (int64_t)(2 * k + 1) * n, make_float2(hi_of(re[k]), hi_of(im[k])));
+      if (row0 + 2 * k < S) red_add2(p + (int64_t)(2 * k) * n, lo_of(re[k]), lo_of(im[k]));
+      if (row0 + 2 * k + 1 < S) red_add2(p + (int64_t)(2 * k + 1) * n, hi_of(re[k]), hi_of(im[k]));
     }
-    if (L::RT && row0 + 2 * L::RP < S) atomicAdd(p + (int64_t)(2 * L::RP) * n, make_float2(tre, tim));
+    if (L::RT && row0 + 2 * L::RP < S) red_add2(p + (int64_t)(2 * L::RP) * n, tre, tim);
   }
   // acc(a) <- acc(a + d); columns a + d >= S start at zero.
   __device__ __forceinline__ void slide(int d, int a) {
@@ -88,9 +88,10 @@ struct Footprint {
 };
 
 // One warp grids the decoded, sorted records [beg, end) of the chunk at byte offset rec_off.
-// Staged table (byte offset tab_off): per class, Lay<S>::CB bytes as described at Lay.
+// Staged table (byte offset tab_off): per class, Lay<S, T>::CB bytes as described at Lay.
 // Decoded record: x, y = c (float bits); z = i0 | j0 << 16; w = class byte offset | conj << 31.
-template <int S>
+// Taps are widened to float32; every product and sum is float32.
+template <int S, class T>
 __device__ __forceinline__ void warp_grid(int tab_off, int rec_off, int beg, int end, float2* __restrict__ grid, int n) {
   using L = Lay<S>;
   const int lane = threadIdx.x & 31;
@@ -106,7 +107,7 @@ __device__ __forceinline__ void warp_grid(int tab_off, int rec_off, int beg, int
 #pragma unroll(L::RP > 1 ? 2 : 4)
   for (int q = beg; q < end; ++q) {
     const uint4 rec = drec[q];
-    Taps<S> tv;
+    Taps<S, T> tv;
     tv.load(tab + (rec.w & 0x7fffffffu), lane);
     if (rec.z != cz) {                             // warp-uniform: a new footprint origin
       const int i0 = rec.z & 0xffff, j0 = rec.z >> 16;
@@ -132,39 +133,40 @@ __device__ __forceinline__ void warp_grid(int tab_off, int rec_off, int beg, int
     const unsigned long long BE = pack2(be, be), DE = pack2(de, de);
 #pragma unroll
     for (int k = 0; k < L::RP; ++k) {
-      const unsigned long long kr = pack2(tv.r[k].x, tv.r[k].y), ki = pack2(tv.i[k].x, tv.i[k].y);
+      const unsigned long long kr = tv.r[k], ki = tv.i[k];
       fp.re[k] = fma2(CR, kr, fp.re[k]);
       fp.re[k] = fma2(BE, ki, fp.re[k]);
       fp.im[k] = fma2(CI, kr, fp.im[k]);
       fp.im[k] = fma2(DE, ki, fp.im[k]);
     }
     if (L::RT) {
-      fp.tre = fmaf(cr, tv.t.x, fp.tre);
-      fp.tre = fmaf(be, tv.t.y, fp.tre);
-      fp.tim = fmaf(cim, tv.t.x, fp.tim);
-      fp.tim = fmaf(de, tv.t.y, fp.tim);
+      fp.tre = fmaf(cr, tv.tr, fp.tre);
+      fp.tre = fmaf(be, tv.ti, fp.tre);
+      fp.tim = fmaf(cim, tv.tr, fp.tim);
+      fp.tim = fmaf(de, tv.ti, fp.tim);
     }
   }
   if (cz == kNoOrigin) return;
   fp.flush(active, grid, n, cj, col0, a, row0);
 }
 
-template <int S>
+template <int S, class T>
 __device__ __noinline__ void grid_segment(const G2Args& a, int p, bool stage, int x0, int y0, int width, uint32_t s0,
                                           uint32_t s1, int cap, int tab_off, int rec_off) {
-  if (stage) stage_table<S>(a.tab + a.tab_off[p], a.g.os, tab_off);
+  if (stage) stage_table<S, T>((const T*)a.tab + a.tab_off[p], a.g.os, tab_off);
   const int keys = width * a.g.tile_y;
   const int warp = threadIdx.x >> 5;
   for (uint32_t c0 = s0; c0 < s1; c0 += (uint32_t)cap) {
     const int m = (int)min((uint32_t)cap, s1 - c0);
-    sort_chunk<S>((const uint4*)a.recs, nullptr, c0, m, x0, y0, width, keys, a.g.os, rec_off);
+    sort_chunk<S, T>((const uint4*)a.recs, nullptr, c0, m, x0, y0, width, keys, a.g.os, rec_off);
     const int beg = (int)((int64_t)m * warp / kWarps), end = (int)((int64_t)m * (warp + 1) / kWarps);
-    warp_grid<S>(tab_off, rec_off, beg, end, a.grid, a.g.n);
+    warp_grid<S, T>(tab_off, rec_off, beg, end, a.grid, a.g.n);
     __syncthreads();
   }
 }
 
 // Grids the records [beg, end) of the (plane, tile)-sorted array, segment by segment.
+template <class T>
 __device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end) {
   int64_t bin = find_bin(a.offsets, a.nbins, beg);
   uint32_t pos = beg;
@@ -176,7 +178,7 @@ __device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end) {
     const int64_t tile = bin - (int64_t)p * a.g.ntiles;
     const int ty = (int)(tile / a.g.ntx), tx = (int)(tile - (int64_t)ty * a.g.ntx);
     const int s = a.g.supp[p];
-    const int rec_off = tab_off + a.g.os * a.g.os * lay_class_bytes(s);
+    const int rec_off = tab_off + a.g.os * a.g.os * lay_class_bytes(s, TabElem<T>::E);
     const int cap = (a.smem_bytes - rec_off) / (int)sizeof(Record);
     int ntiles = 1;
     const uint32_t seg_end = segment_end(a.offsets, a.nbins, bin, tx, a.g.ntx, pos, end, cap, a.group_tiles, &ntiles);
@@ -187,7 +189,7 @@ __device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end) {
     switch (s) {
 #define WP_SEG_CASE(N)                                                                   \
   case N:                                                                                \
-    grid_segment<N>(a, p, stage, x0, y0, width, pos, seg_end, cap, tab_off, rec_off);    \
+    grid_segment<N, T>(a, p, stage, x0, y0, width, pos, seg_end, cap, tab_off, rec_off);    \
     break;
       WP_SEG_CASE(1) WP_SEG_CASE(2) WP_SEG_CASE(3) WP_SEG_CASE(4) WP_SEG_CASE(5) WP_SEG_CASE(6) WP_SEG_CASE(7)
       WP_SEG_CASE(8) WP_SEG_CASE(9) WP_SEG_CASE(10) WP_SEG_CASE(11) WP_SEG_CASE(12) WP_SEG_CASE(13)
@@ -200,9 +202,10 @@ __device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end) {
   }
 }
 
+template <class T>
 __global__ void __launch_bounds__(kThreads, 1) k_grid_v2(G2Args a) {
   for_each_unit(a.offsets, a.costoff, a.nbins, a.nunits, a.work,
-                [&](uint32_t beg, uint32_t end) { grid_range(a, beg, end); });
+                [&](uint32_t beg, uint32_t end) { grid_range<T>(a, beg, end); });
 }
 
 }  // namespace
@@ -211,7 +214,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_v2(G2Args a) {
 // is outside the kernel's limits (then the baseline kernel of grid.cu runs).
 size_t grid_v2_smem(const wp_ctx* ctx, int* group_tiles) {
   const int smax = *std::max_element(ctx->supp.begin(), ctx->supp.end());
-  if (smax > kMaxS || ctx->prm.table_type != WP_TABLE_F32) return 0;
+  if (smax > kMaxS) return 0;
+  const int e = ctx->prm.table_type == WP_TABLE_F32 ? 4 : 2;
   const int os = ctx->prm.oversample;
   const int tx = ctx->geo.tile_x, ty = ctx->geo.tile_y;
   if ((int64_t)tx * ty > kMaxKeys) return 0;
@@ -220,7 +224,7 @@ size_t grid_v2_smem(const wp_ctx* ctx, int* group_tiles) {
     return 0;
   const size_t bytes = (size_t)optin - 1024;        // room for the static scan scratch
   size_t tab = 0;
-  for (int sp : ctx->supp) tab = std::max(tab, (size_t)os * os * lay_class_bytes(sp));
+  for (int sp : ctx->supp) tab = std::max(tab, (size_t)os * os * lay_class_bytes(sp, e));
   if ((size_t)kCountsBytes + tab + (size_t)kMinChunk * sizeof(Record) > bytes) return 0;
   *group_tiles = std::max(1, std::min(8, kMaxKeys / (tx * ty)));
   return bytes;
@@ -237,7 +241,7 @@ cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used
   a.costoff = ctx->d_costoff;
   a.nbins = ctx->nbins;
   a.g = ctx->geo;
-  a.tab = (const float2*)ctx->d_tab;
+  a.tab = ctx->d_tab;
   a.tab_off = ctx->d_tab_off;
   a.grid = grid;
   a.smem_bytes = (int)smem;
@@ -246,9 +250,17 @@ cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used
   a.work = ctx->d_work;
   cudaError_t e;
   if ((e = launch_bin_costs(ctx, s))) return e;
-  if ((e = cudaFuncSetAttribute(k_grid_v2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-  k_grid_v2<<<ctx->nsm, kThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  auto run = [&](auto kern) -> cudaError_t {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err) return err;
+    kern<<<ctx->nsm, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+  };
+  switch (ctx->prm.table_type) {
+    case WP_TABLE_F16: return run(k_grid_v2<__half2>);
+    case WP_TABLE_BF16: return run(k_grid_v2<__nv_bfloat162>);
+    default: return run(k_grid_v2<float2>);
+  }
 }
 
 }  // namespace wp

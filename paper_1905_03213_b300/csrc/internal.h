@@ -76,6 +76,7 @@ struct wp_ctx {
   // device state owned by the context
   double* d_legendre = nullptr;
   double* d_taper_img = nullptr;       // [N] t(x_i), x_i = 2 (i - N/2) / N
+  float* d_taper_inv = nullptr;        // [N] 1 / t(x_i)
   double* d_taper_lat = nullptr;       // [(M+1)/2] t(x_j), j = 0 .. (M-1)/2
   double* d_cos = nullptr;             // [os M] cos(2 pi r / (os M))
   double2* d_screen = nullptr;         // [Nw][H][H] screen quadrant (j, j' >= 0)
@@ -148,6 +149,7 @@ cudaError_t launch_degrid(wp_ctx* ctx, const float2* grid, float2* vis_out, cons
 cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* vis_out, const uint32_t* index,
                              cudaStream_t s, bool* used);
 // imaging (image.cu)
-cudaError_t launch_image_post(const float2* spectrum, const double* sum_w, const double* taper_img,
+cudaError_t launch_taper_inverse(const double* taper_img, float* inv, int32_t n, cudaStream_t s);
+cudaError_t launch_image_post(const float2* spectrum, const double* sum_w, const float* inv_taper,
                               int32_t taper_correct, float* image, int32_t n, cudaStream_t s);
 }  // namespace wp

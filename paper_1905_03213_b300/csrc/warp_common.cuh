@@ -5,6 +5,8 @@
 // definition has internal linkage.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -23,20 +25,44 @@ constexpr int kUnitsPerCta = 8;                              // work units per C
 
 
 // Lane layout for support S: G row groups of S lanes; lane g*S + a holds rows g*R ..
-// g*R + R - 1 of footprint column a, as RP row pairs and RT (0/1) single tail row. The staged
-// table of one oversampling class holds, per row pair k, a block of 32 float2 {kr(2k), kr(2k+1)}
-// then a block of 32 float2 {ki(2k), ki(2k+1)} (one entry per lane), then for the tail row a
-// block of 32 float2 {kr, ki}. Lanes beyond G*S have all-zero entries.
+// g*R + R - 1 of footprint column a, as RP row pairs and RT (0/1) single tail row.
+//
+// Staged table of one oversampling class, for tap components of E bytes (4: f32, 2: f16/bf16),
+// one entry per lane in 32-lane blocks (lanes beyond G*S hold zeros):
+//   f32:     per row pair k a block of float2 {kr(2k), kr(2k+1)} then a block of float2
+//            {ki(2k), ki(2k+1)}; then for the tail row a block of float2 {kr, ki}.
+//   f16/bf16: per row pair k one block of 8-byte entries {kr(2k), kr(2k+1), ki(2k), ki(2k+1)};
+//            then for the tail row a block of 4-byte entries {kr, ki}.
+// Either way a lane reads 8 bytes per row pair and load instruction.
 __host__ __device__ constexpr int lay_rows(int s) { return (s + 32 / s - 1) / (32 / s); }
 __host__ __device__ constexpr int lay_groups(int s) { return (s + lay_rows(s) - 1) / lay_rows(s); }
-// staged bytes per oversampling class: 2 RP blocks of 32 x float2, then one more if RT
-__host__ __device__ constexpr int lay_class_bytes(int s) { return (lay_rows(s) / 2) * 512 + (lay_rows(s) & 1) * 256; }
+// staged bytes per oversampling class
+__host__ __device__ constexpr int lay_class_bytes(int s, int e) {
+  return ((lay_rows(s) / 2) * 128 + (lay_rows(s) & 1) * 64) * e;
+}
 
-template <int S>
+template <class T>
+struct TabElem;  // component size of a stored table element (a complex tap)
+template <>
+struct TabElem<float2> {
+  static constexpr int E = 4;
+};
+template <>
+struct TabElem<__half2> {
+  static constexpr int E = 2;
+};
+template <>
+struct TabElem<__nv_bfloat162> {
+  static constexpr int E = 2;
+};
+
+template <int S, class T = float2>
 struct Lay {
   static constexpr int R = lay_rows(S), G = lay_groups(S), NL = G * S;
   static constexpr int RP = R / 2, RT = R & 1, RPA = RP > 0 ? RP : 1;
-  static constexpr int CB = lay_class_bytes(S);
+  static constexpr int E = TabElem<T>::E;
+  static constexpr int PB = 128 * E;           // bytes of one row pair's blocks
+  static constexpr int CB = lay_class_bytes(S, E);
 };
 
 __device__ __forceinline__ unsigned char* dyn_smem() {
@@ -122,34 +148,85 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
+// Vector reduction (no return value) of two floats into global memory: *p += (x, y).
+__device__ __forceinline__ void red_add2(float2* p, float x, float y) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(x), "f"(y) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long shfl_down2(unsigned long long v, int d) {
   const uint32_t lo = __shfl_down_sync(0xffffffffu, (uint32_t)v, d);
   const uint32_t hi = __shfl_down_sync(0xffffffffu, (uint32_t)(v >> 32), d);
   return (unsigned long long)lo | ((unsigned long long)hi << 32);
 }
 
-// This lane's taps of one record: RP row pairs as {kr(2k), kr(2k+1)} and {ki(2k), ki(2k+1)}, and the tail.
-template <int S>
+__device__ __forceinline__ float2 to_float2(__half2 h) { return __half22float2(h); }
+__device__ __forceinline__ float2 to_float2(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+template <class T>
+__device__ __forceinline__ T bits_as(uint32_t u) {
+  T t;
+  memcpy(&t, &u, 4);
+  return t;
+}
+
+// This lane's taps of one record as float32: RP row pairs packed {kr(2k), kr(2k+1)} and
+// {ki(2k), ki(2k+1)} for f32x2 FMAs, and the tail row.
+template <int S, class T = float2>
 struct Taps {
-  float2 r[Lay<S>::RPA], i[Lay<S>::RPA];
-  float2 t;
+  unsigned long long r[Lay<S, T>::RPA], i[Lay<S, T>::RPA];
+  float tr, ti;
   // Lanes beyond the layout (lane >= NL) read their all-zero table entries.
   __device__ __forceinline__ void load(const unsigned char* cls_base, int lane) {
-    using L = Lay<S>;
+    using L = Lay<S, T>;
+    if constexpr (L::E == 4) {
 #pragma unroll
-    for (int k = 0; k < L::RP; ++k) {
-      r[k] = *(const float2*)(cls_base + k * 512 + lane * 8);
-      i[k] = *(const float2*)(cls_base + k * 512 + 256 + lane * 8);
+      for (int k = 0; k < L::RP; ++k) {
+        r[k] = *(const unsigned long long*)(cls_base + k * L::PB + lane * 8);
+        i[k] = *(const unsigned long long*)(cls_base + k * L::PB + 256 + lane * 8);
+      }
+      if (L::RT) {
+        const float2 t = *(const float2*)(cls_base + L::RP * L::PB + lane * 8);
+        tr = t.x;
+        ti = t.y;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < L::RP; ++k) {
+        const uint2 v = *(const uint2*)(cls_base + k * L::PB + lane * 8);
+        const float2 a = to_float2(bits_as<T>(v.x)), b = to_float2(bits_as<T>(v.y));
+        r[k] = pack2(a.x, a.y);
+        i[k] = pack2(b.x, b.y);
+      }
+      if (L::RT) {
+        const float2 t = to_float2(bits_as<T>(*(const uint32_t*)(cls_base + L::RP * L::PB + lane * 4)));
+        tr = t.x;
+        ti = t.y;
+      }
     }
-    if (L::RT) t = *(const float2*)(cls_base + L::RP * 512 + lane * 8);
   }
 };
 
-// Stages one plane's table (src: layout [oy*os+ox][a][b]) in the lane layout of Lay<S> at
-// byte offset tab_off of the dynamic shared memory.
-template <int S>
-__device__ __forceinline__ void stage_table(const float2* __restrict__ src, int os, int tab_off) {
-  using L = Lay<S>;
+__device__ __forceinline__ float2 tap_float2(float2 v) { return v; }
+__device__ __forceinline__ float2 tap_float2(__half2 v) { return __half22float2(v); }
+__device__ __forceinline__ float2 tap_float2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+__device__ __forceinline__ uint32_t pack_pair(__half2, float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  uint32_t u;
+  memcpy(&u, &h, 4);
+  return u;
+}
+__device__ __forceinline__ uint32_t pack_pair(__nv_bfloat162, float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  uint32_t u;
+  memcpy(&u, &h, 4);
+  return u;
+}
+
+// Stages one plane's table (src: stored layout [oy*os+ox][a][b] of T) in the lane layout of
+// Lay<S, T> at byte offset tab_off of the dynamic shared memory. 16-bit components are copied
+// exactly (each is representable after the round trip through float32).
+template <int S, class T = float2>
+__device__ __forceinline__ void stage_table(const T* __restrict__ src, int os, int tab_off) {
+  using L = Lay<S, T>;
   constexpr int kPer = L::RP + L::RT;           // entries per lane and class
   const int ncls = os * os;
   unsigned char* dst = dyn_smem() + tab_off;
@@ -159,15 +236,20 @@ __device__ __forceinline__ void stage_table(const float2* __restrict__ src, int 
     const int g = lane / S, col = lane - g * S;
     const bool active = lane < L::NL;
     const int b0 = g * L::R + 2 * k;
-    const float2* s = src + ((int64_t)cls * S + col) * S;
-    const float2 v0 = (active && b0 < S) ? __ldg(s + b0) : make_float2(0.f, 0.f);
-    unsigned char* d = dst + cls * L::CB + k * 512 + lane * 8;
+    const T* s = src + ((int64_t)cls * S + col) * S;
+    const float2 v0 = (active && b0 < S) ? tap_float2(s[b0]) : make_float2(0.f, 0.f);
+    unsigned char* base = dst + cls * L::CB + k * L::PB;
     if (k < L::RP) {
-      const float2 v1 = (active && b0 + 1 < S) ? __ldg(s + b0 + 1) : make_float2(0.f, 0.f);
-      *(float2*)d = make_float2(v0.x, v1.x);
-      *(float2*)(d + 256) = make_float2(v0.y, v1.y);
+      const float2 v1 = (active && b0 + 1 < S) ? tap_float2(s[b0 + 1]) : make_float2(0.f, 0.f);
+      if constexpr (L::E == 4) {
+        *(float2*)(base + lane * 8) = make_float2(v0.x, v1.x);
+        *(float2*)(base + 256 + lane * 8) = make_float2(v0.y, v1.y);
+      } else {
+        *(uint2*)(base + lane * 8) = make_uint2(pack_pair(T{}, v0.x, v1.x), pack_pair(T{}, v0.y, v1.y));
+      }
     } else {
-      *(float2*)d = v0;
+      if constexpr (L::E == 4) *(float2*)(base + lane * 8) = v0;
+      else *(uint32_t*)(base + lane * 4) = pack_pair(T{}, v0.x, v0.y);
     }
   }
 }
@@ -179,11 +261,11 @@ __device__ __forceinline__ void stage_table(const float2* __restrict__ src, int 
 // With `index` (a gridding plan's visibility index per record, partner flag in bit 31) the
 // Hermitian partners are left out and x becomes the visibility index. Returns the number of
 // records sorted; counts[key] (the shared counters at offset 0) is then the end of each key.
-template <int S>
+template <int S, class T = float2>
 __device__ __forceinline__ int sort_chunk(const uint4* __restrict__ grecs, const uint32_t* __restrict__ index,
                                           uint32_t c0, int m, int x0, int y0, int width, int keys, int os,
                                           int rec_off) {
-  using L = Lay<S>;
+  using L = Lay<S, T>;
   uint32_t* counts = (uint32_t*)dyn_smem();
   uint4* drec = (uint4*)(dyn_smem() + rec_off);
   for (int k = threadIdx.x; k <= keys; k += kThreads) counts[k] = 0u;

@@ -185,7 +185,7 @@ void wp_destroy(wp_ctx* ctx) {
     cudaEventDestroy(it.second.second);
   }
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
-  void* ptrs[] = {ctx->d_legendre, ctx->d_taper_img, ctx->d_taper_lat, ctx->d_cos,      ctx->d_screen,
+  void* ptrs[] = {ctx->d_legendre, ctx->d_taper_img, ctx->d_taper_inv, ctx->d_taper_lat, ctx->d_cos,      ctx->d_screen,
                   ctx->d_stage,    ctx->d_quad,      ctx->d_tab64,     ctx->d_tab,      ctx->d_supp,
                   ctx->d_wplane,   ctx->d_tab_off,   ctx->d_tab64_off, ctx->d_quad_off, ctx->d_nu,
                   ctx->d_counts,   ctx->d_offsets,   ctx->d_cursor,    ctx->d_partials, ctx->d_chan,
@@ -290,7 +290,7 @@ int wp_create(wp_ctx** out, const wp_params* p) {
   for (int i = 0; i < q.n_w; ++i) dmax = std::max(dmax, ctx->supp[i] * q.oversample / 2 + 1);
   const size_t tab_bytes = (q.table_type == WP_TABLE_F32 ? 8 : 4) * (size_t)ctx->tab_elems;
   bool ok = dalloc(&ctx->d_legendre, ctx->legendre.size()) == cudaSuccess &&
-            dalloc(&ctx->d_taper_img, (size_t)q.n) == cudaSuccess && dalloc(&ctx->d_taper_lat, (size_t)h) == cudaSuccess &&
+            dalloc(&ctx->d_taper_img, (size_t)q.n) == cudaSuccess && dalloc(&ctx->d_taper_inv, (size_t)q.n) == cudaSuccess && dalloc(&ctx->d_taper_lat, (size_t)h) == cudaSuccess &&
             dalloc(&ctx->d_cos, (size_t)q.oversample * ctx->m) == cudaSuccess &&
             dalloc(&ctx->d_screen, (size_t)q.n_w * h * h) == cudaSuccess &&
             dalloc(&ctx->d_stage, (size_t)q.n_w * h * dmax) == cudaSuccess &&
@@ -324,6 +324,7 @@ int wp_create(wp_ctx** out, const wp_params* p) {
   const int ncoef = (int)ctx->legendre.size();
   if (wp::launch_taper_eval(ctx->d_legendre, ncoef, ctx->d_taper_img, q.n, 1, q.n, 0) != cudaSuccess ||
       wp::launch_taper_eval(ctx->d_legendre, ncoef, ctx->d_taper_lat, h, 0, ctx->m, 0) != cudaSuccess ||
+      wp::launch_taper_inverse(ctx->d_taper_img, ctx->d_taper_inv, q.n, 0) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     return bail(WP_ECUDA, std::string("taper evaluation failed: ") + cudaGetErrorString(cudaGetLastError()));
   }
@@ -431,7 +432,7 @@ int wp_fft_to_image(wp_ctx* ctx, void* grid, const double* sum_w, int32_t taper_
   }
   {
     Phase ph(ctx, WP_PHASE_IMAGE, s);
-    WP_CUDA(ctx, wp::launch_image_post((const float2*)grid, sum_w, ctx->d_taper_img, taper_correct, image,
+    WP_CUDA(ctx, wp::launch_image_post((const float2*)grid, sum_w, ctx->d_taper_inv, taper_correct, image,
                                        ctx->prm.n, s));
     ++ctx->launches;
   }

@@ -213,18 +213,19 @@ def test_repeat_runs_agree(torch_cuda):
 
 
 # ---------------------------------------------------------------- degridding
-@pytest.mark.parametrize("which", ["parity", "random"])
-def test_degrid_parity(torch_cuda, which):
+@pytest.mark.parametrize("which,table", [("parity", "f32"), ("random", "f32"), ("random", "f16"), ("random", "bf16")])
+def test_degrid_parity(torch_cuda, which, table):
+    """Degridding against the float64 oracle; f16/bf16 tables within the mixed-precision tolerances."""
     import torch
     case = parity_case() if which == "parity" else random_case(n=128, nrow=1200, nchan=3, s_min=5, s_max=12)
     crd = oracle.coords(case.uvw, case.freqs, case.prm)
     gh = synth.random_grid(case.prm.n, 9)
     ref = oracle.degrid(crd, gh.astype(np.complex128), case.tables, case.prm).reshape(case.vis.shape)
-    wp = make_wproj(case)
+    wp = make_wproj(case, table=table)
     uvw, f, _, _ = to_dev(case)
     out = wp.degrid(uvw, f, torch.from_numpy(gh).cuda()).cpu().numpy()
     e, _ = peak_rel(out, ref)
-    assert e < 1e-5, e
+    assert e < TOL_IMAGE[table], e
     np.testing.assert_array_equal(out.ravel()[~crd["keep"]], 0)
 
 
