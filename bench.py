@@ -22,6 +22,7 @@ max over ranks of the timed region; scaling "weak".
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -228,8 +229,9 @@ def run_gpu(args):
         "degrid_kernel": {"ms": degrid_ms, "vis_per_s": kept_degrid / (degrid_ms * 1e-3),
                           "taps_per_s": taps_degrid / (degrid_ms * 1e-3), "taps": taps_degrid},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                     "frac": achieved / peak_fp32, "traffic": None,
-                     "kernel": "k_grid_v2 (register-accumulating gridding scatter, 8 flop per tap)" if args.table == "f32" else "k_grid_v1 (gridding scatter, 8 flop per tap)",
+                     "frac": achieved / peak_fp32, "traffic": profiled_traffic(args.table, args.rows),
+                     "traffic_note": f"DRAM bytes per launch from the ncu summary in {GRID_PROFILE}",
+                     "kernel": f"k_grid_v2<{args.table}> (warp-synchronous register-accumulating gridding scatter, 8 flop per tap)",
                      "peak_note": "FP32 FMA peak derived from unit counts (148 SMs x 128 lanes x 2 x 2.032 GHz)",
                      "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / (grid_ms * 1e-3) / 1e9,
                              "peak_gbs": peaks.get("hbm_gbs"), "peak_note": "of measured"}},
@@ -245,6 +247,33 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return out
+
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+GRID_KERNEL_SOURCES = ("paper_1905_03213_b300/csrc/grid2.cu", "paper_1905_03213_b300/csrc/warp_common.cuh")
+GRID_PROFILE = "profiles/k_grid_v2_fp32_workload.md"
+
+
+def profiled_traffic(table: str, rows: int):
+    """DRAM bytes of one gridding launch on the full fp32 workload, as the committed ncu summary
+    states them, or None when the summary was taken on other kernel sources (or another case)."""
+    if rows or table != "f32":
+        return None
+    h = hashlib.sha256()
+    try:
+        for p in GRID_KERNEL_SOURCES:
+            with open(os.path.join(ROOT, p), "rb") as f:
+                h.update(f.read())
+        text = open(os.path.join(ROOT, GRID_PROFILE)).read()
+    except OSError:
+        return None
+    fields = dict(line.split(": ", 1) for line in text.splitlines() if ": " in line and line.split(": ", 1)[0].isascii())
+    if fields.get("kernel_source_sha256[:16] (grid2.cu + warp_common.cuh)", "").strip() != h.hexdigest()[:16]:
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch[f32]"].strip())
+    except (KeyError, ValueError):
+        return None
 
 
 def run_e2e(wp, uvw, vis, wt, freq, grid, sum_w, ndrop, pred, image, cfg, args, stream, units):
@@ -356,7 +385,7 @@ def main():
     ap.add_argument("--config", default="fp32")
     ap.add_argument("--table", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--tile", default="", help="origin tile WxH, e.g. 64x32")
-    ap.add_argument("--cpu-vis", type=int, default=1_000_000, help="visibilities (rows x channels) in the CPU sample")
+    ap.add_argument("--cpu-vis", type=int, default=6_000_000, help="visibilities (rows x channels) in the CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rows", type=int, default=0, help="use only the first ROWS rows (profiling captures)")
