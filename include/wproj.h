@@ -166,6 +166,17 @@ int wp_degrid_last(wp_ctx* ctx, const void* grid, void* vis_out, void* stream);
 int wp_fft_to_image(wp_ctx* ctx, void* grid, const double* sum_w, int32_t taper_correct,
                     float* image, void* stream);
 
+/* The adjoint of wp_fft_to_image (image -> grid), the first half of the forward model
+ * image -> grid -> visibilities whose second half is wp_degrid:
+ *   grid[h][g] = sum_{j,i} X[j][i] exp(-2 pi i ((g-N/2)(i-N/2) + (h-N/2)(j-N/2))/N),
+ *   X[j][i] = image[j][i] / (sum_w * t(x_i) t(x_j))   (no t factor if !taper_correct),
+ * so that <wp_fft_to_image(G), image> = Re <G, wp_image_to_grid(image)> for real images.
+ *   image device [N][N] float32 (read only); sum_w device float64, or NULL for 1;
+ *   grid  device [N][N] float2 (overwritten; the in-place FFT buffer).
+ * Uses the context's cuFFT plan. Errors: WP_EINVAL, WP_ECUDA. */
+int wp_image_to_grid(wp_ctx* ctx, const float* image, const double* sum_w, int32_t taper_correct,
+                     void* grid, void* stream);
+
 /* ---- inspection and tracing ---- */
 
 /* Per-plane full support S_p and w_p (host memory, Nw entries each). Synchronous. */

@@ -17,7 +17,7 @@ _TABLES = {"f32": WP_TABLE_F32, "f16": WP_TABLE_F16, "bf16": WP_TABLE_BF16}
 # every function declared in include/wproj.h
 SYMBOLS = ("wp_create", "wp_destroy", "wp_last_error", "wp_make_wkernels", "wp_grid", "wp_degrid",
            "wp_fft_to_image", "wp_plane_info", "wp_coords", "wp_wkernel_export", "wp_wkernel_norm",
-           "wp_profile", "wp_profile_read", "wp_taper_eval_host", "wp_grid_noalloc", "wp_degrid_last")
+           "wp_profile", "wp_profile_read", "wp_taper_eval_host", "wp_grid_noalloc", "wp_degrid_last", "wp_image_to_grid")
 PHASES = ("wkernels", "plan", "grid", "degrid", "fft", "image")
 
 
@@ -50,6 +50,7 @@ def _load():
     L.wp_degrid.argtypes = [P, P, P, P, I64, I32, P, P]
     L.wp_degrid_last.argtypes = [P, P, P, P]
     L.wp_fft_to_image.argtypes = [P, P, P, I32, P, P]
+    L.wp_image_to_grid.argtypes = [P, P, P, I32, P, P]
     L.wp_plane_info.argtypes = [P, P, P]
     L.wp_coords.argtypes = [P, P, P, I64, I32, I32, P, P]
     L.wp_wkernel_export.argtypes = [P, I32, I32, P, I64]
@@ -198,6 +199,19 @@ class WProj:
         self._check(lib.wp_fft_to_image(self._h, _ptr(grid), _ptr(sum_w), 1 if taper_correct else 0, _ptr(image),
                                         self._stream(stream)), "wp_fft_to_image")
         return image
+
+    def image_to_grid(self, image, sum_w=None, taper_correct: bool = True, grid=None, stream=None):
+        """Adjoint of fft_to_image: the [N, N] complex64 grid of a real [N, N] float32 image."""
+        import torch
+        _dev_tensor(image, torch.float32, "image", (self.n, self.n))
+        if sum_w is not None:
+            _dev_tensor(sum_w, torch.float64, "sum_w")
+        if grid is None:
+            grid = torch.empty((self.n, self.n), dtype=torch.complex64, device=image.device)
+        _dev_tensor(grid, torch.complex64, "grid", (self.n, self.n))
+        self._check(lib.wp_image_to_grid(self._h, _ptr(image), _ptr(sum_w), 1 if taper_correct else 0, _ptr(grid),
+                                         self._stream(stream)), "wp_image_to_grid")
+        return grid
 
     def coords(self, uvw, freq, hermitian_pairs: bool = False, stream=None):
         """[ngridded, 8] int32: U, V, plane, conj, keep, i0, j0, ox | oy << 16."""

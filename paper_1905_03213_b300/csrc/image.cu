@@ -37,7 +37,44 @@ __global__ void k_image_post(const float2* __restrict__ f, const double* __restr
   image[(int64_t)j * n + i] = sgn * v * scale;
 }
 
+// The adjoint direction (wp_image_to_grid): with z[j][i] = (-1)^(i + j) X[j][i], the centred
+// forward transform is G[h][g] = (-1)^(g + h) DFT2(z)[h][g] (same parity argument as above), so
+// the pre-kernel forms z, cuFFT runs forward in place and the post-kernel flips the signs.
+__global__ void k_image_pre(const float* __restrict__ image, const double* __restrict__ sum_w,
+                            const float* __restrict__ inv_taper, int32_t taper_correct, float2* __restrict__ z,
+                            int32_t n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n) return;
+  float scale = sum_w ? 1.0f / (float)*sum_w : 1.0f;
+  if (taper_correct) scale *= inv_taper[i] * inv_taper[j];
+  const float sgn = ((i + j) & 1) ? -1.f : 1.f;
+  z[(int64_t)j * n + i] = make_float2(sgn * scale * image[(int64_t)j * n + i], 0.f);
+}
+
+__global__ void k_checker_sign(float2* __restrict__ g, int32_t n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n || !((i + j) & 1)) return;
+  float2* p = &g[(int64_t)j * n + i];
+  const float2 v = *p;
+  *p = make_float2(-v.x, -v.y);
+}
+
 }  // namespace
+
+cudaError_t launch_image_pre(const float* image, const double* sum_w, const float* inv_taper, int32_t taper_correct,
+                             float2* z, int32_t n, cudaStream_t s) {
+  dim3 grid((n + 255) / 256, n);
+  k_image_pre<<<grid, 256, 0, s>>>(image, sum_w, inv_taper, taper_correct, z, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_checker_sign(float2* g, int32_t n, cudaStream_t s) {
+  dim3 grid((n + 255) / 256, n);
+  k_checker_sign<<<grid, 256, 0, s>>>(g, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_taper_inverse(const double* taper_img, float* inv, int32_t n, cudaStream_t s) {
   k_taper_inverse<<<(n + 255) / 256, 256, 0, s>>>(taper_img, inv, n);

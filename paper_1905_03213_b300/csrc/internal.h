@@ -150,6 +150,9 @@ cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* vis_out, c
                              cudaStream_t s, bool* used);
 // imaging (image.cu)
 cudaError_t launch_taper_inverse(const double* taper_img, float* inv, int32_t n, cudaStream_t s);
+cudaError_t launch_image_pre(const float* image, const double* sum_w, const float* inv_taper, int32_t taper_correct,
+                             float2* z, int32_t n, cudaStream_t s);
+cudaError_t launch_checker_sign(float2* g, int32_t n, cudaStream_t s);
 cudaError_t launch_image_post(const float2* spectrum, const double* sum_w, const float* inv_taper,
                               int32_t taper_correct, float* image, int32_t n, cudaStream_t s);
 }  // namespace wp

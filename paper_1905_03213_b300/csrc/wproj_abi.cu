@@ -414,17 +414,26 @@ int wp_degrid_last(wp_ctx* ctx, const void* grid, void* vis_out, void* stream) {
   return WP_OK;
 }
 
-int wp_fft_to_image(wp_ctx* ctx, void* grid, const double* sum_w, int32_t taper_correct, float* image, void* stream) {
-  if (!ctx) return WP_EINVAL;
-  if (!grid || !sum_w || !image) return fail(ctx, WP_EINVAL, "grid, sum_w and image must not be NULL");
-  cudaStream_t s = (cudaStream_t)stream;
-  WP_CUDA(ctx, cudaSetDevice(ctx->prm.device));
+namespace {
+// The context's N x N C2C plan, created on first use, bound to stream s.
+int ensure_fft(wp_ctx* ctx, cudaStream_t s) {
   if (!ctx->have_fft) {
     if (cufftPlan2d(&ctx->fft, ctx->prm.n, ctx->prm.n, CUFFT_C2C) != CUFFT_SUCCESS)
       return fail(ctx, WP_ECUDA, "cufftPlan2d failed");
     ctx->have_fft = true;
   }
   if (cufftSetStream(ctx->fft, s) != CUFFT_SUCCESS) return fail(ctx, WP_ECUDA, "cufftSetStream failed");
+  return WP_OK;
+}
+}  // namespace
+
+int wp_fft_to_image(wp_ctx* ctx, void* grid, const double* sum_w, int32_t taper_correct, float* image, void* stream) {
+  if (!ctx) return WP_EINVAL;
+  if (!grid || !sum_w || !image) return fail(ctx, WP_EINVAL, "grid, sum_w and image must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  WP_CUDA(ctx, cudaSetDevice(ctx->prm.device));
+  int rc = ensure_fft(ctx, s);
+  if (rc) return rc;
   {
     Phase ph(ctx, WP_PHASE_FFT, s);
     if (cufftExecC2C(ctx->fft, (cufftComplex*)grid, (cufftComplex*)grid, CUFFT_INVERSE) != CUFFT_SUCCESS)
@@ -436,6 +445,23 @@ int wp_fft_to_image(wp_ctx* ctx, void* grid, const double* sum_w, int32_t taper_
                                        ctx->prm.n, s));
     ++ctx->launches;
   }
+  return WP_OK;
+}
+
+int wp_image_to_grid(wp_ctx* ctx, const float* image, const double* sum_w, int32_t taper_correct, void* grid,
+                     void* stream) {
+  if (!ctx) return WP_EINVAL;
+  if (!grid || !image) return fail(ctx, WP_EINVAL, "image and grid must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  WP_CUDA(ctx, cudaSetDevice(ctx->prm.device));
+  int rc = ensure_fft(ctx, s);
+  if (rc) return rc;
+  Phase ph(ctx, WP_PHASE_FFT, s);
+  WP_CUDA(ctx, wp::launch_image_pre(image, sum_w, ctx->d_taper_inv, taper_correct, (float2*)grid, ctx->prm.n, s));
+  if (cufftExecC2C(ctx->fft, (cufftComplex*)grid, (cufftComplex*)grid, CUFFT_FORWARD) != CUFFT_SUCCESS)
+    return fail(ctx, WP_ECUDA, "cufftExecC2C failed");
+  WP_CUDA(ctx, wp::launch_checker_sign((float2*)grid, ctx->prm.n, s));
+  ctx->launches += 2;
   return WP_OK;
 }
 
