@@ -95,9 +95,13 @@ struct wp_ctx {
   // binning
   wp::Geometry geo{};
   int64_t nbins = 0;
-  uint32_t* d_counts = nullptr;        // [nbins]
+  // Each bin's counter is split into nsub sub-counters (visibility index mod nsub), so that the
+  // atomics of a dense bin spread over nsub addresses; a bin's records stay contiguous.
+  int32_t nsub_log2 = 0;
+  uint32_t* d_counts = nullptr;        // [nbins * nsub] histogram (also scratch for the work estimates)
+  uint32_t* d_suboff = nullptr;        // [nbins * nsub + 1] exclusive prefix sums of the sub-counters
   uint32_t* d_offsets = nullptr;       // [nbins + 1], exclusive prefix sums, total at the end
-  uint32_t* d_cursor = nullptr;        // [nbins]
+  uint32_t* d_cursor = nullptr;        // [nbins * nsub]
   uint32_t* d_partials = nullptr;      // scan partials
   uint32_t* d_costoff = nullptr;       // [nbins + 1] exclusive prefix sums of per-bin work estimates
   uint32_t* d_partials2 = nullptr;     // scan partials of the work estimates

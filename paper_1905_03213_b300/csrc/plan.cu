@@ -138,18 +138,10 @@ __device__ __forceinline__ Products products(const double* __restrict__ uvw, con
   return p;
 }
 
-// Warp-aggregated atomicAdd of 1 on counter[key] for the active lanes with key != ~0u.
-// Returns the per-lane slot (old value + rank among lanes with the same key).
-__device__ __forceinline__ uint32_t aggregated_increment(uint32_t* counter, uint32_t key) {
-  const unsigned active = __activemask();
-  const unsigned peers = __match_any_sync(active, key);
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  const unsigned rank = __popc(peers & ((1u << lane) - 1));
-  uint32_t base = 0;
-  if (lane == leader && key != 0xffffffffu) base = atomicAdd(&counter[key], (uint32_t)__popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  return base + rank;
+// Sub-counter of visibility k's bin: bins are split into 2^nsub_log2 sub-counters by the low
+// bits of k, so that the atomics of one dense bin land on several addresses.
+__device__ __forceinline__ uint32_t sub_bin(uint32_t bin, int64_t k, int32_t nsub_log2) {
+  return (bin << nsub_log2) | ((uint32_t)k & ((1u << nsub_log2) - 1u));
 }
 
 __global__ void k_channel_factors(const double* __restrict__ freq, int32_t nchan, double os_l,
@@ -168,7 +160,8 @@ __global__ void __launch_bounds__(256) k_histogram(const double* __restrict__ uv
                                                    const float* __restrict__ weight, int64_t nvis, int32_t nchan,
                                                    int32_t pairs, Geometry g, uint32_t* __restrict__ counts,
                                                    unsigned long long* __restrict__ dropped,
-                                                   double* __restrict__ wsum, int32_t* __restrict__ rounded) {
+                                                   double* __restrict__ wsum, int32_t* __restrict__ rounded,
+                                                   int32_t nsub_log2) {
   double my_w = 0.0;
   unsigned long long my_drop = 0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nvis; k += (int64_t)gridDim.x * blockDim.x) {
@@ -178,8 +171,7 @@ __global__ void __launch_bounds__(256) k_histogram(const double* __restrict__ uv
     int nkept = 0;
     for (int h = 0; h <= pairs; ++h) {
       const Coord c = make_coord(rd, h == 1, g);
-      const uint32_t key = c.keep ? bin_of(c, g) : 0xffffffffu;
-      aggregated_increment(counts, key);
+      if (c.keep) atomicAdd(&counts[sub_bin(bin_of(c, g), k, nsub_log2)], 1u);
       nkept += c.keep ? 1 : 0;
     }
     my_drop += (unsigned long long)(pairs + 1 - nkept);
@@ -216,7 +208,7 @@ __global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ uvw,
                                                  int64_t nvis, int32_t nchan, int32_t pairs, int32_t for_degrid,
                                                  Geometry g, uint32_t* __restrict__ cursor,
                                                  Record* __restrict__ records, const int32_t* __restrict__ rounded,
-                                                 uint32_t* __restrict__ index) {
+                                                 uint32_t* __restrict__ index, int32_t nsub_log2) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nvis; k += (int64_t)gridDim.x * blockDim.x) {
     Rounded rd;
     if (rounded) {
@@ -233,9 +225,8 @@ __global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ uvw,
     }
     for (int h = 0; h <= pairs; ++h) {
       const Coord c = make_coord(rd, h == 1, g);
-      const uint32_t key = c.keep ? bin_of(c, g) : 0xffffffffu;
-      const uint32_t slot = aggregated_increment(cursor, key);
       if (c.keep) {
+        const uint32_t slot = atomicAdd(&cursor[sub_bin(bin_of(c, g), k, nsub_log2)], 1u);
         Record rec;
         if (for_degrid) {
           rec.x = (uint32_t)k;
@@ -367,6 +358,13 @@ __global__ void k_coords_out(const double* __restrict__ uvw, const double* __res
   }
 }
 
+// offsets[b] = suboff[b << nsub_log2] for b <= nbins (the first sub-counter of each bin).
+__global__ void k_gather_offsets(const uint32_t* __restrict__ suboff, int64_t nbins, int32_t nsub_log2,
+                                 uint32_t* __restrict__ offsets) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b <= nbins) offsets[b] = suboff[b << nsub_log2];
+}
+
 int grid_blocks(int64_t work, int nsm) {
   const int64_t want = (work + 255) / 256;
   const int64_t cap = (int64_t)nsm * 16;
@@ -385,7 +383,8 @@ cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const
                         int32_t nchan, bool pairs, bool for_degrid, cudaStream_t s) {
   const int64_t nvis = nrow * nchan;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(ctx->d_counts, 0, sizeof(uint32_t) * ctx->nbins, s))) return e;
+  const int64_t nsub = ctx->nbins << ctx->nsub_log2;
+  if ((e = cudaMemsetAsync(ctx->d_counts, 0, sizeof(uint32_t) * nsub, s))) return e;
   if ((e = cudaMemsetAsync(ctx->d_dropped, 0, sizeof(unsigned long long), s))) return e;
   if ((e = cudaMemsetAsync(ctx->d_wsum, 0, sizeof(double), s))) return e;
   const int blocks = grid_blocks(nvis, ctx->nsm);
@@ -394,23 +393,28 @@ cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const
   // a gridding plan also records each record's visibility index, for wp_degrid_last
   const size_t nrec = (size_t)nvis * (pairs ? 2 : 1);
   uint32_t* index = (!for_degrid && ctx->rec_index.bytes >= nrec * 4) ? (uint32_t*)ctx->rec_index.ptr : nullptr;
-  ctx->launches += 3 + (nvis > 0 ? 2 : 0);  // prefix sum (3), histogram and scatter
+  ctx->launches += 4 + (nvis > 0 ? 2 : 0);  // prefix sum (3), bin offsets, histogram and scatter
   if (nvis > 0) {
     k_histogram<<<blocks, 256, 0, s>>>(uvw, ctx->d_chan, for_degrid ? nullptr : weight, nvis, nchan, pairs ? 1 : 0,
-                                       ctx->geo, ctx->d_counts, ctx->d_dropped, ctx->d_wsum, rounded);
+                                       ctx->geo, ctx->d_counts, ctx->d_dropped, ctx->d_wsum, rounded,
+                                       ctx->nsub_log2);
     if ((e = cudaGetLastError())) return e;
   }
-  const int64_t tiles = (ctx->nbins + kScanTile - 1) / kScanTile;
-  k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(ctx->d_counts, ctx->nbins, ctx->d_offsets, ctx->d_partials);
+  const int64_t tiles = (nsub + kScanTile - 1) / kScanTile;
+  k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(ctx->d_counts, nsub, ctx->d_suboff, ctx->d_partials);
   if ((e = cudaGetLastError())) return e;
   k_scan_partials<<<1, kScanThreads, 0, s>>>(ctx->d_partials, tiles);
   if ((e = cudaGetLastError())) return e;
-  k_scan_finish<<<(unsigned)((ctx->nbins + 255) / 256), 256, 0, s>>>(ctx->d_offsets, ctx->d_cursor, ctx->nbins,
-                                                                     ctx->d_partials, tiles);
+  k_scan_finish<<<(unsigned)((nsub + 255) / 256), 256, 0, s>>>(ctx->d_suboff, ctx->d_cursor, nsub, ctx->d_partials,
+                                                               tiles);
+  if ((e = cudaGetLastError())) return e;
+  k_gather_offsets<<<(unsigned)((ctx->nbins + 256) / 256), 256, 0, s>>>(ctx->d_suboff, ctx->nbins, ctx->nsub_log2,
+                                                                          ctx->d_offsets);
   if ((e = cudaGetLastError())) return e;
   if (nvis > 0) {
     k_scatter<<<blocks, 256, 0, s>>>(uvw, ctx->d_chan, vis, weight, nvis, nchan, pairs ? 1 : 0, for_degrid ? 1 : 0,
-                                     ctx->geo, ctx->d_cursor, (Record*)ctx->records.ptr, rounded, index);
+                                     ctx->geo, ctx->d_cursor, (Record*)ctx->records.ptr, rounded, index,
+                                     ctx->nsub_log2);
     if ((e = cudaGetLastError())) return e;
   }
   return cudaSuccess;

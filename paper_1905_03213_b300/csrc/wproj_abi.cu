@@ -189,7 +189,7 @@ void wp_destroy(wp_ctx* ctx) {
                   ctx->d_stage,    ctx->d_quad,      ctx->d_tab64,     ctx->d_tab,      ctx->d_supp,
                   ctx->d_wplane,   ctx->d_tab_off,   ctx->d_tab64_off, ctx->d_quad_off, ctx->d_nu,
                   ctx->d_counts,   ctx->d_offsets,   ctx->d_cursor,    ctx->d_partials, ctx->d_chan,
-                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2, ctx->d_work, ctx->rounded.ptr, ctx->rec_index.ptr};
+                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2, ctx->d_work, ctx->rounded.ptr, ctx->rec_index.ptr, ctx->d_suboff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -283,7 +283,10 @@ int wp_create(wp_ctx** out, const wp_params* p) {
   g.wscale = q.n_w > 1 ? (double)(q.n_w - 1) / q.w_max : 0.0;
   ctx->nbins = g.ntiles * q.n_w;
   if (ctx->nbins > (int64_t)4096 * 4096) return bail(WP_EINVAL, "too many bins (n_w * tiles > 2^24): use larger tiles");
-  const int64_t scan_tiles = (ctx->nbins + 4095) / 4096;
+  // sub-counters per bin: up to 16, keeping nbins * nsub <= 2^24 (the prefix sum's reach)
+  while (ctx->nsub_log2 < 4 && (ctx->nbins << (ctx->nsub_log2 + 1)) <= (int64_t)4096 * 4096) ++ctx->nsub_log2;
+  const int64_t nsubbins = ctx->nbins << ctx->nsub_log2;
+  const int64_t scan_tiles = (nsubbins + 4095) / 4096;
 
   const int h = (ctx->m + 1) / 2;
   int dmax = 0;
@@ -301,9 +304,10 @@ int wp_create(wp_ctx** out, const wp_params* p) {
             dalloc(&ctx->d_tab_off, (size_t)q.n_w) == cudaSuccess &&
             dalloc(&ctx->d_tab64_off, (size_t)q.n_w) == cudaSuccess &&
             dalloc(&ctx->d_quad_off, (size_t)q.n_w) == cudaSuccess && dalloc(&ctx->d_nu, 1) == cudaSuccess &&
-            dalloc(&ctx->d_counts, (size_t)ctx->nbins) == cudaSuccess &&
+            dalloc(&ctx->d_counts, (size_t)nsubbins) == cudaSuccess &&
+            dalloc(&ctx->d_suboff, (size_t)nsubbins + 1) == cudaSuccess &&
             dalloc(&ctx->d_offsets, (size_t)ctx->nbins + 1) == cudaSuccess &&
-            dalloc(&ctx->d_cursor, (size_t)ctx->nbins) == cudaSuccess &&
+            dalloc(&ctx->d_cursor, (size_t)nsubbins) == cudaSuccess &&
             dalloc(&ctx->d_partials, (size_t)scan_tiles + 1) == cudaSuccess &&
             dalloc(&ctx->d_costoff, (size_t)ctx->nbins + 1) == cudaSuccess &&
             dalloc(&ctx->d_partials2, (size_t)scan_tiles + 1) == cudaSuccess &&

@@ -283,9 +283,9 @@ def test_profile_counts_phases_and_launches(torch_cuda):
     ms, cnt, launches = wp.profile_read()
     assert cnt == {"wkernels": 1, "plan": 2, "grid": 1, "degrid": 1, "fft": 1, "image": 1}
     assert all(v > 0 for v in ms.values())
-    # 6 kernel-table + (1 channel + 5 plan + 4 work-estimate scan + 1 grid + 1 scalars)
-    # + (1 channel + 5 plan + 4 work-estimate scan + 1 degrid) + 1 image
-    assert launches == 30
+    # 6 kernel-table + (1 channel + 6 plan + 4 work-estimate scan + 1 grid + 1 scalars)
+    # + (1 channel + 6 plan + 4 work-estimate scan + 1 degrid) + 1 image
+    assert launches == 32
     # degridding the gridded visibilities again reuses wp_grid's binning: no plan phase
     g, sw, _ = wp.grid(uvw, f, vis, wt)
     wp.profile_read()
