@@ -135,6 +135,47 @@ int wp_grid_noalloc(wp_ctx* ctx, const double* uvw, const double* freq, const vo
                     const float* weight, int64_t nrow, int32_t nchan, int32_t flags, void* grid,
                     double* sum_w, int64_t* n_dropped, void* stream);
 
+/* ---- many gridding jobs in one launch ---- */
+
+/* One gridding job: the arguments of one wp_grid call. Each job has its own context (its own
+ * geometry, kernel tables and binning); all contexts on one device, no context twice. */
+typedef struct wp_job {
+  wp_ctx* ctx;
+  const double* uvw;     /* device [nrow][3] */
+  const double* freq;    /* device [nchan] */
+  const void* vis;       /* device [nrow][nchan] float2 */
+  const float* weight;   /* device [nrow][nchan] or NULL */
+  int64_t nrow;
+  int32_t nchan;
+  int32_t flags;         /* WP_ACCUMULATE | WP_HERMITIAN_PAIRS */
+  void* grid;            /* device [N][N] float2 of the job's context */
+  double* sum_w;         /* device, or NULL */
+  int64_t* n_dropped;    /* device, or NULL */
+} wp_job;
+
+typedef struct wp_batch wp_batch;
+
+/* A batch of gridding jobs (imaging jobs of different visibility counts, grid sizes, supports,
+ * oversampling and plane counts). Creation validates the jobs, allocates every per-job scratch
+ * buffer and the batch's descriptors, and fixes the job table: the pointers and sizes are read
+ * once, the data behind them is read at every wp_batch_grid. Each job's context must have its
+ * kernel tables (wp_make_wkernels). Synchronous. Errors: WP_EINVAL (bad job, shared context,
+ * mixed devices), WP_ESTATE, WP_ENOMEM, WP_ECUDA; the message is in the failing job's context. */
+int wp_batch_create(const wp_job* jobs, int32_t njobs, wp_batch** out);
+
+/* Grids every job of the batch, with the results of calling wp_grid on each: the jobs'
+ * coordinates and binning (per-job launches), then ONE persistent launch of the warp gridding
+ * kernel over the work of all jobs whose geometry it takes and whose table type is that of the
+ * first such job (the other jobs run the baseline kernel one by one). Makes no allocation and
+ * no host synchronisation, so a stream capture of it replays as a CUDA graph. Errors: WP_ECUDA. */
+int wp_batch_grid(wp_batch* batch, void* stream);
+
+/* Number of jobs in the batch's persistent launch. */
+int32_t wp_batch_fused_jobs(const wp_batch* batch);
+
+/* Frees the batch (not the jobs' contexts or buffers). */
+void wp_batch_destroy(wp_batch* batch);
+
 /* Degridding, the adjoint of wp_grid with unit weights (Sec. 2 names gridding and
  * degridding as the pair being accelerated):
  *   vis_out[r][c] = sum_{a,b} grid[j0+b][i0+a] * conj(K_k[...])   (same coordinates and taps;

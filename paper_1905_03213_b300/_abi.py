@@ -17,7 +17,8 @@ _TABLES = {"f32": WP_TABLE_F32, "f16": WP_TABLE_F16, "bf16": WP_TABLE_BF16}
 # every function declared in include/wproj.h
 SYMBOLS = ("wp_create", "wp_destroy", "wp_last_error", "wp_make_wkernels", "wp_grid", "wp_degrid",
            "wp_fft_to_image", "wp_plane_info", "wp_coords", "wp_wkernel_export", "wp_wkernel_norm",
-           "wp_profile", "wp_profile_read", "wp_taper_eval_host", "wp_grid_noalloc", "wp_degrid_last", "wp_image_to_grid")
+           "wp_profile", "wp_profile_read", "wp_taper_eval_host", "wp_grid_noalloc", "wp_degrid_last", "wp_image_to_grid",
+           "wp_batch_create", "wp_batch_grid", "wp_batch_fused_jobs", "wp_batch_destroy")
 PHASES = ("wkernels", "plan", "grid", "degrid", "fft", "image")
 
 
@@ -25,6 +26,13 @@ class WProjError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"wproj error {code}: {msg}")
         self.code = code
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("uvw", ctypes.c_void_p), ("freq", ctypes.c_void_p),
+                ("vis", ctypes.c_void_p), ("weight", ctypes.c_void_p), ("nrow", ctypes.c_int64),
+                ("nchan", ctypes.c_int32), ("flags", ctypes.c_int32), ("grid", ctypes.c_void_p),
+                ("sum_w", ctypes.c_void_p), ("n_dropped", ctypes.c_void_p)]
 
 
 class Params(ctypes.Structure):
@@ -51,6 +59,12 @@ def _load():
     L.wp_degrid_last.argtypes = [P, P, P, P]
     L.wp_fft_to_image.argtypes = [P, P, P, I32, P, P]
     L.wp_image_to_grid.argtypes = [P, P, P, I32, P, P]
+    L.wp_batch_create.argtypes = [ctypes.POINTER(Job), I32, ctypes.POINTER(P)]
+    L.wp_batch_grid.argtypes = [P, P]
+    L.wp_batch_fused_jobs.argtypes = [P]
+    L.wp_batch_fused_jobs.restype = I32
+    L.wp_batch_destroy.argtypes = [P]
+    L.wp_batch_destroy.restype = None
     L.wp_plane_info.argtypes = [P, P, P]
     L.wp_coords.argtypes = [P, P, P, I64, I32, I32, P, P]
     L.wp_wkernel_export.argtypes = [P, I32, I32, P, I64]
@@ -257,3 +271,90 @@ class WProj:
         self._check(lib.wp_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data, ctypes.byref(nl)),
                     "wp_profile_read")
         return dict(zip(PHASES, ms.tolist())), dict(zip(PHASES, cnt.tolist())), nl.value
+
+
+class WBatch:
+    """Many gridding jobs (each a WProj with its own geometry) gridded by wp_batch_grid: the jobs'
+    coordinates and binning, then one persistent gridding launch over all of them.
+
+    jobs: list of dicts with keys wp, uvw, freq, vis, and optionally weight, grid, sum_w,
+    n_dropped, hermitian_pairs, accumulate. The tensors are fixed at creation (kept referenced
+    here); their contents are read at every grid() call, so a captured graph can be replayed on
+    new data written into the same tensors."""
+
+    def __init__(self, jobs):
+        import torch
+        self._keep = []
+        arr = (Job * len(jobs))()
+        self.outputs = []
+        for i, j in enumerate(jobs):
+            wp = j["wp"]
+            uvw, freq, vis = j["uvw"], j["freq"], j["vis"]
+            _dev_tensor(uvw, torch.float64, "uvw")
+            _dev_tensor(freq, torch.float64, "freq")
+            nrow, nchan = uvw.shape[0], freq.shape[0]
+            _dev_tensor(vis, torch.complex64, "vis", (nrow, nchan))
+            weight = j.get("weight")
+            if weight is not None:
+                _dev_tensor(weight, torch.float32, "weight", (nrow, nchan))
+            dev = uvw.device
+            grid = j.get("grid")
+            if grid is None:
+                grid = torch.empty((wp.n, wp.n), dtype=torch.complex64, device=dev)
+            _dev_tensor(grid, torch.complex64, "grid", (wp.n, wp.n))
+            sum_w = j.get("sum_w")
+            if sum_w is None:
+                sum_w = torch.zeros(1, dtype=torch.float64, device=dev)
+            nd = j.get("n_dropped")
+            if nd is None:
+                nd = torch.zeros(1, dtype=torch.int64, device=dev)
+            flags = (WP_ACCUMULATE if j.get("accumulate") else 0) | (WP_HERMITIAN_PAIRS if j.get("hermitian_pairs") else 0)
+            arr[i] = Job(wp._h, uvw.data_ptr(), freq.data_ptr(), vis.data_ptr(),
+                         None if weight is None else weight.data_ptr(), nrow, nchan, flags, grid.data_ptr(),
+                         sum_w.data_ptr(), nd.data_ptr())
+            self._keep += [wp, uvw, freq, vis, weight, grid, sum_w, nd]
+            self.outputs.append((grid, sum_w, nd))
+        h = ctypes.c_void_p()
+        rc = lib.wp_batch_create(arr, len(jobs), ctypes.byref(h))
+        if rc != WP_OK:
+            msg = ""
+            for j in jobs:
+                m = lib.wp_last_error(j["wp"]._h)
+                if m:
+                    msg = m.decode()
+            raise WProjError(rc, f"wp_batch_create: {msg}")
+        self._h = h
+        self._jobs = arr
+
+    @property
+    def fused_jobs(self) -> int:
+        return int(lib.wp_batch_fused_jobs(self._h))
+
+    def grid(self, stream=None):
+        import torch
+        s = torch.cuda.current_stream() if stream is None else stream
+        rc = lib.wp_batch_grid(self._h, ctypes.c_void_p(s.cuda_stream))
+        if rc != WP_OK:
+            raise WProjError(rc, "wp_batch_grid")
+        return self.outputs
+
+    def capture(self):
+        """A torch.cuda.CUDAGraph replaying grid() (one eager run first warms every buffer)."""
+        import torch
+        self.grid()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.grid()
+        return g
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.wp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

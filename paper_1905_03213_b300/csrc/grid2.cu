@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "internal.h"
 #include "warp_common.cuh"
@@ -208,6 +209,72 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_v2(G2Args a) {
                 [&](uint32_t beg, uint32_t end) { grid_range<T>(a, beg, end); });
 }
 
+// ---- many jobs in one persistent launch (wp_batch_grid) ----
+
+struct BatchArgs {
+  const G2Args* jobs;        // [njobs] per-job arguments (device), smem_bytes shared
+  const uint64_t* jobcost;   // [njobs + 1] prefix sums of each job's total estimated work
+  int njobs;
+  int nunits;
+  uint32_t* work;            // [2]: next unit, finished CTAs (both zero between launches)
+};
+
+// jobcost[j + 1] = jobcost[j] + (total estimated work of job j), one thread.
+__global__ void k_job_costs(const G2Args* __restrict__ jobs, int njobs, uint64_t* __restrict__ jobcost) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint64_t c = 0;
+  jobcost[0] = 0;
+  for (int j = 0; j < njobs; ++j) {
+    c += jobs[j].costoff[jobs[j].nbins];
+    jobcost[j + 1] = c;
+  }
+}
+
+// Record position of cost position x (0 <= x <= ctotal) of one job: the monotone map of the
+// single-job schedule.
+__device__ __forceinline__ uint32_t job_split(const G2Args& a, uint64_t x) {
+  const uint32_t total = a.offsets[a.nbins];
+  const uint32_t ctotal = a.costoff[a.nbins];
+  if (x >= ctotal) return total;
+  const int64_t b = find_bin(a.costoff, a.nbins, (uint32_t)x);
+  const uint32_t c0 = a.costoff[b], cb = a.costoff[b + 1] - c0;
+  const uint32_t n = a.offsets[b + 1] - a.offsets[b];
+  return a.offsets[b] + (uint32_t)(((uint64_t)(x - c0) * n) / cb);
+}
+
+// Work unit u covers [C u / nunits, C (u + 1) / nunits) of the concatenated work of all jobs
+// (C = jobcost[njobs]); the part inside job j is gridded with job j's arguments. Units are
+// taken from the counter from the last one down.
+template <class T>
+__global__ void __launch_bounds__(kThreads, 1) k_grid_batch(BatchArgs b) {
+  __shared__ int unit;
+  const uint64_t ctot = b.jobcost[b.njobs];
+  for (;;) {
+    if (threadIdx.x == 0) unit = b.nunits - 1 - (int)atomicAdd(&b.work[0], 1u);
+    __syncthreads();
+    const int u = unit;
+    __syncthreads();
+    if (u < 0) break;
+    const uint64_t x0 = ctot * (uint64_t)u / (uint64_t)b.nunits, x1 = ctot * (uint64_t)(u + 1) / (uint64_t)b.nunits;
+    int j = 0;
+    while (j + 1 < b.njobs && b.jobcost[j + 1] <= x0) ++j;
+    for (; j < b.njobs && b.jobcost[j] < x1; ++j) {
+      const G2Args a = b.jobs[j];
+      const uint64_t lo = max(x0, b.jobcost[j]) - b.jobcost[j], hi = min(x1, b.jobcost[j + 1]) - b.jobcost[j];
+      const uint32_t beg = job_split(a, lo), end = job_split(a, hi);
+      if (beg < end) grid_range<T>(a, beg, end);
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&b.work[1], 1u) == gridDim.x - 1) {
+      b.work[0] = 0u;
+      b.work[1] = 0u;
+      __threadfence();
+    }
+  }
+}
+
 }  // namespace
 
 // Dynamic shared memory of the launch (the device's opt-in maximum), or 0 when the geometry
@@ -261,6 +328,60 @@ cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used
     case WP_TABLE_BF16: return run(k_grid_v2<__nv_bfloat162>);
     default: return run(k_grid_v2<float2>);
   }
+}
+
+}  // namespace wp
+
+namespace wp {
+
+size_t grid_job_desc_bytes() { return sizeof(G2Args); }
+
+// Host-side arguments of one job for the multi-job launch (job's context, grid and the launch's
+// shared-memory size); the job's own work-estimate scan must have run before the launch.
+void grid_job_desc(wp_ctx* ctx, float2* grid, size_t smem, void* out) {
+  int group = 1;
+  grid_v2_smem(ctx, &group);
+  G2Args a;
+  a.recs = (const Record*)ctx->records.ptr;
+  a.offsets = ctx->d_offsets;
+  a.costoff = ctx->d_costoff;
+  a.nbins = ctx->nbins;
+  a.g = ctx->geo;
+  a.tab = ctx->d_tab;
+  a.tab_off = ctx->d_tab_off;
+  a.grid = grid;
+  a.smem_bytes = (int)smem;
+  a.group_tiles = group;
+  a.nunits = 0;
+  a.work = nullptr;
+  memcpy(out, &a, sizeof(a));
+}
+
+cudaError_t prepare_grid_batch(int table_type, size_t smem) {
+  switch (table_type) {
+    case WP_TABLE_F16: return cudaFuncSetAttribute(k_grid_batch<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    case WP_TABLE_BF16: return cudaFuncSetAttribute(k_grid_batch<__nv_bfloat162>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    default: return cudaFuncSetAttribute(k_grid_batch<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+}
+
+cudaError_t launch_grid_batch(const void* d_jobs, int njobs, uint64_t* d_jobcost, uint32_t* d_work, int table_type,
+                              size_t smem, int nsm, cudaStream_t s) {
+  k_job_costs<<<1, 32, 0, s>>>((const G2Args*)d_jobs, njobs, d_jobcost);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  BatchArgs b;
+  b.jobs = (const G2Args*)d_jobs;
+  b.jobcost = d_jobcost;
+  b.njobs = njobs;
+  b.nunits = nsm * kUnitsPerCta;
+  b.work = d_work;
+  switch (table_type) {
+    case WP_TABLE_F16: k_grid_batch<__half2><<<nsm, kThreads, smem, s>>>(b); break;
+    case WP_TABLE_BF16: k_grid_batch<__nv_bfloat162><<<nsm, kThreads, smem, s>>>(b); break;
+    default: k_grid_batch<float2><<<nsm, kThreads, smem, s>>>(b); break;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace wp

@@ -146,6 +146,14 @@ cudaError_t launch_coords(wp_ctx* ctx, const double* uvw, int64_t nrow, int32_t 
 cudaError_t launch_grid(wp_ctx* ctx, float2* grid, cudaStream_t s);
 // register-accumulating gridding kernel (grid2.cu); *used = false when the geometry is outside its limits
 cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used);
+// shared memory the warp gridding kernel needs for ctx (0: outside its limits)
+size_t grid_v2_smem(const wp_ctx* ctx, int* group_tiles);
+// multi-job persistent gridding (grid2.cu): per-job descriptors, then one launch over all jobs
+size_t grid_job_desc_bytes();
+void grid_job_desc(wp_ctx* ctx, float2* grid, size_t smem, void* out);
+cudaError_t prepare_grid_batch(int table_type, size_t smem);
+cudaError_t launch_grid_batch(const void* d_jobs, int njobs, uint64_t* d_jobcost, uint32_t* d_work, int table_type,
+                              size_t smem, int nsm, cudaStream_t s);
 // index: the gridding plan's visibility indices (degrid that plan's records), or nullptr
 cudaError_t launch_degrid(wp_ctx* ctx, const float2* grid, float2* vis_out, const uint32_t* index,
                           cudaStream_t s);

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <memory>
 #include <string>
 
 #include "internal.h"
@@ -596,3 +597,138 @@ int wp_taper_eval_host(double c, const double* x, int64_t n, double* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- batches of gridding jobs
+
+struct wp_batch {
+  std::vector<wp_job> jobs;
+  std::vector<int> fused;               // jobs in the persistent launch
+  int table_type = WP_TABLE_F32;
+  size_t smem = 0;
+  int device = 0;
+  int nsm = 0;
+  void* d_desc = nullptr;               // [fused] per-job kernel arguments
+  uint64_t* d_jobcost = nullptr;        // [fused + 1]
+  uint32_t* d_work = nullptr;           // [2]
+};
+
+void wp_batch_destroy(wp_batch* b) {
+  if (!b) return;
+  if (b->d_desc) cudaFree(b->d_desc);
+  if (b->d_jobcost) cudaFree(b->d_jobcost);
+  if (b->d_work) cudaFree(b->d_work);
+  delete b;
+}
+
+int32_t wp_batch_fused_jobs(const wp_batch* b) { return b ? (int32_t)b->fused.size() : 0; }
+
+int wp_batch_create(const wp_job* jobs, int32_t njobs, wp_batch** out) {
+  if (!out) return WP_EINVAL;
+  *out = nullptr;
+  if (njobs < 1 || !jobs) return WP_EINVAL;
+  std::unique_ptr<wp_batch, void (*)(wp_batch*)> b(new wp_batch, wp_batch_destroy);
+  for (int32_t i = 0; i < njobs; ++i) {
+    const wp_job& j = jobs[i];
+    if (!j.ctx) return WP_EINVAL;
+    wp_ctx* ctx = j.ctx;
+    for (int32_t k = 0; k < i; ++k)
+      if (jobs[k].ctx == ctx) return fail(ctx, WP_EINVAL, "wp_batch_create: a context appears in two jobs");
+    if (ctx->prm.device != jobs[0].ctx->prm.device)
+      return fail(ctx, WP_EINVAL, "wp_batch_create: all jobs must be on one device");
+    if (j.flags & ~(WP_ACCUMULATE | WP_HERMITIAN_PAIRS)) return fail(ctx, WP_EINVAL, "unknown flag bits");
+    if (!j.grid) return fail(ctx, WP_EINVAL, "grid must not be NULL");
+    if (j.nrow > 0 && !j.vis) return fail(ctx, WP_EINVAL, "vis must not be NULL");
+    const int pairs = (j.flags & WP_HERMITIAN_PAIRS) ? 1 : 0;
+    int rc = check_vis_args(ctx, j.uvw, j.freq, j.nrow, j.nchan, pairs);
+    if (rc) return rc;
+    if (!ctx->have_kernels) return fail(ctx, WP_ESTATE, "wp_make_wkernels has not been called");
+    WP_CUDA(ctx, cudaSetDevice(ctx->prm.device));
+    if ((rc = ensure_channels(ctx, j.nchan))) return rc;
+    const size_t nv = (size_t)j.nrow * j.nchan, ng = nv * (pairs ? 2 : 1);
+    if ((rc = ensure_buffer(ctx, ctx->records, std::max<size_t>(ng, 1) * sizeof(wp::Record), "records"))) return rc;
+    if ((rc = ensure_buffer(ctx, ctx->rounded, std::max<size_t>(nv, 1) * 12, "coordinate scratch"))) return rc;
+    b->jobs.push_back(j);
+  }
+  wp_ctx* c0 = jobs[0].ctx;
+  b->device = c0->prm.device;
+  b->nsm = c0->nsm;
+  // the persistent launch takes the jobs the warp kernel takes, of the first such job's table type
+  for (int32_t i = 0; i < njobs; ++i) {
+    int group = 1;
+    const size_t sm = wp::grid_v2_smem(jobs[i].ctx, &group);
+    if (!sm) continue;
+    if (b->fused.empty()) b->table_type = jobs[i].ctx->prm.table_type;
+    if (jobs[i].ctx->prm.table_type != b->table_type) continue;
+    b->fused.push_back(i);
+    b->smem = std::max(b->smem, sm);
+  }
+  if (!b->fused.empty()) {
+    const size_t db = wp::grid_job_desc_bytes();
+    std::vector<unsigned char> host(db * b->fused.size());
+    for (size_t f = 0; f < b->fused.size(); ++f) {
+      const wp_job& j = jobs[b->fused[f]];
+      wp::grid_job_desc(j.ctx, (float2*)j.grid, b->smem, host.data() + f * db);
+    }
+    if (cudaMalloc(&b->d_desc, host.size()) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_jobcost, sizeof(uint64_t) * (b->fused.size() + 1)) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_work, 2 * sizeof(uint32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c0, WP_ENOMEM, "wp_batch_create: device allocation failed");
+    }
+    if (cudaMemcpy(b->d_desc, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_work, 0, 2 * sizeof(uint32_t)) != cudaSuccess ||
+        wp::prepare_grid_batch(b->table_type, b->smem) != cudaSuccess) {
+      const cudaError_t e = cudaGetLastError();
+      return fail(c0, WP_ECUDA, std::string("wp_batch_create: ") + cudaGetErrorString(e));
+    }
+  }
+  *out = b.release();
+  return WP_OK;
+}
+
+int wp_batch_grid(wp_batch* b, void* stream) {
+  if (!b) return WP_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  WP_CUDA(b->jobs[0].ctx, cudaSetDevice(b->device));
+  std::vector<char> is_fused(b->jobs.size(), 0);
+  for (int f : b->fused) is_fused[f] = 1;
+  // coordinates and binning of every job; the baseline kernel for jobs outside the launch
+  for (size_t i = 0; i < b->jobs.size(); ++i) {
+    const wp_job& j = b->jobs[i];
+    wp_ctx* ctx = j.ctx;
+    const int pairs = (j.flags & WP_HERMITIAN_PAIRS) ? 1 : 0;
+    ctx->have_grid_plan = false;
+    const int32_t n = ctx->prm.n;
+    if (!(j.flags & WP_ACCUMULATE)) WP_CUDA(ctx, cudaMemsetAsync(j.grid, 0, sizeof(float2) * (size_t)n * n, s));
+    if (j.nrow > 0) {
+      WP_CUDA(ctx, wp::launch_channel_factors(j.freq, j.nchan, ctx->geo.os_l, ctx->geo.wscale, ctx->d_chan, s));
+      ++ctx->launches;
+    }
+    {
+      Phase ph(ctx, WP_PHASE_PLAN, s);
+      WP_CUDA(ctx, wp::launch_plan(ctx, j.uvw, (const float2*)j.vis, j.weight, j.nrow, j.nchan, pairs != 0, false, s));
+    }
+    if (is_fused[i]) {
+      WP_CUDA(ctx, wp::launch_bin_costs(ctx, s));
+    } else {
+      Phase ph(ctx, WP_PHASE_GRID, s);
+      WP_CUDA(ctx, wp::launch_grid(ctx, (float2*)j.grid, s));
+    }
+  }
+  if (!b->fused.empty()) {
+    wp_ctx* c0 = b->jobs[b->fused[0]].ctx;
+    Phase ph(c0, WP_PHASE_GRID, s);
+    WP_CUDA(c0, wp::launch_grid_batch(b->d_desc, (int)b->fused.size(), b->d_jobcost, b->d_work, b->table_type,
+                                      b->smem, b->nsm, s));
+    c0->launches += 2;
+  }
+  for (const wp_job& j : b->jobs) {
+    if (j.sum_w || j.n_dropped) {
+      k_store_scalars<<<1, 1, 0, s>>>(j.ctx->d_wsum, j.ctx->d_dropped, j.sum_w, (long long*)j.n_dropped,
+                                      (j.flags & WP_ACCUMULATE) ? 1 : 0);
+      WP_CUDA(j.ctx, cudaGetLastError());
+      ++j.ctx->launches;
+    }
+  }
+  return WP_OK;
+}
