@@ -33,6 +33,8 @@ struct D2Args {
   Geometry g;
   const void* tab;          // stored tables (f32, f16 or bf16 taps), layout [plane][oy*os+ox][a][b]
   const int64_t* tab_off;
+  const unsigned char* lanetab;   // lane-order tables of the planes with S > 16 (global)
+  const int64_t* lanetab_off;     // [Nw] byte offset of each plane in lanetab (-1: none)
   const float2* grid;
   float2* out;              // visibilities in caller order (record x = caller index)
   const uint32_t* index;    // gridding plan's visibility index per record (partners flagged), or nullptr
@@ -46,7 +48,7 @@ struct D2Args {
 // mod 8, so rows two apart fall in opposite halves of the 32 banks.
 __host__ __device__ constexpr int sub_pitch(int cols) { return cols + ((12 - cols % 8) % 8); }
 // Rows staged for support s: the tile rows plus every row a lane of the layout can address.
-__host__ __device__ constexpr int sub_rows(int tile_y, int s) { return tile_y + lay_groups(s) * lay_rows(s) - 1; }
+__host__ __device__ constexpr int sub_rows(int tile_y, int s) { return tile_y + lay_span(s) - 1; }
 __host__ __device__ constexpr int sub_bytes(int tile_x, int tile_y, int group, int s) {
   return sub_rows(tile_y, s) * sub_pitch(group * tile_x + s - 1) * 8;
 }
@@ -74,16 +76,20 @@ __device__ __forceinline__ void batch_reduce(float (&v)[NB], int lane) {
 }
 
 // One warp degrids the decoded, sorted records [beg, end) of the chunk at byte offset rec_off
-// from the grid region staged at sub_off (pitch entries per row, origin (sx0, sy0)).
+// from the grid region staged at sub_off (pitch entries per row, origin (sx0, sy0)). Table as
+// in the gridding kernel (staged at tab_off, or the global copy gtab for S > 16, row half h);
+// with two row halves each warp adds its half of every visibility to the (zeroed) output.
 template <int S, class T>
-__device__ __forceinline__ void warp_degrid(int tab_off, int sub_off, int pitch, int sx0, int sy0, int rec_off,
-                                            int beg, int end, float2* __restrict__ out) {
-  using L = Lay<S>;
+__device__ __forceinline__ void warp_degrid(int tab_off, const unsigned char* gtab, int h, int sub_off, int pitch,
+                                            int sx0, int sy0, int rec_off, int beg, int end,
+                                            float2* __restrict__ out) {
+  using L = Lay<S, T>;
   constexpr int NB = L::RP <= 2 ? 32 : 16;
   const int lane = threadIdx.x & 31;
   const int g = lane / S, a = lane - g * S;
-  const int row0 = lane < L::NL ? g * L::R : 0;   // lanes beyond the layout read (zero-tap) cells of row 0
-  const unsigned char* tab = dyn_smem() + tab_off;
+  // lanes beyond the layout read (zero-tap) cells of the half's first row
+  const int row0 = L::kGlobalTable ? h * L::R : (lane < L::NL ? g * L::R : 0);
+  const unsigned char* tab = L::kGlobalTable ? gtab + h * L::HB : dyn_smem() + tab_off;
   const float2* sub = (const float2*)(dyn_smem() + sub_off);
   const uint4* drec = (const uint4*)(dyn_smem() + rec_off);
   unsigned long long GR[L::RPA], GI[L::RPA], NGI[L::RPA];   // cells: re, im, -im of row pairs
@@ -141,7 +147,10 @@ __device__ __forceinline__ void warp_degrid(int tab_off, int sub_off, int pitch,
     }
     batch_reduce<NB>(pre, lane);
     batch_reduce<NB>(pim, lane);
-    if (lane < NB && b0 + lane < end) out[drec[b0 + lane].x] = make_float2(pre[0], pim[0]);
+    if (lane < NB && b0 + lane < end) {
+      if constexpr (L::H > 1) red_add2(&out[drec[b0 + lane].x], pre[0], pim[0]);
+      else out[drec[b0 + lane].x] = make_float2(pre[0], pim[0]);
+    }
   }
 }
 
@@ -149,8 +158,12 @@ template <int S, class T>
 __device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, int x0, int y0, int width,
                                             uint32_t s0, uint32_t s1, int cap, int tab_off, int sub_off,
                                             int rec_off) {
-  using L = Lay<S>;
-  if (stage) stage_table<S, T>((const T*)a.tab + a.tab_off[p], a.g.os, tab_off);
+  using L = Lay<S, T>;
+  if constexpr (!L::kGlobalTable) {
+    if (stage) stage_table<S, T>((const T*)a.tab + a.tab_off[p], a.g.os, tab_off);
+  }
+  const unsigned char* gtab = L::kGlobalTable ? a.lanetab + a.lanetab_off[p] : nullptr;
+  constexpr int kPieces = kWarps / L::H;            // warps of a row-half pair share a piece
   // the grid region under the segment's footprints (cells outside the grid read as zero)
   const int cols = width + S - 1, rows = sub_rows(a.g.tile_y, S), pitch = sub_pitch(cols);
   float2* sub = (float2*)(dyn_smem() + sub_off);
@@ -164,11 +177,11 @@ __device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, 
   for (uint32_t c0 = s0; c0 < s1; c0 += (uint32_t)cap) {
     const int m = (int)min((uint32_t)cap, s1 - c0);
     const int kept = sort_chunk<S, T>((const uint4*)a.recs, a.index, c0, m, x0, y0, width, keys, a.g.os, rec_off);
-    const int beg = (int)((int64_t)kept * warp / kWarps), end = (int)((int64_t)kept * (warp + 1) / kWarps);
-    warp_degrid<S, T>(tab_off, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
+    const int piece = warp / L::H, h = warp % L::H;
+    const int beg = (int)((int64_t)kept * piece / kPieces), end = (int)((int64_t)kept * (piece + 1) / kPieces);
+    warp_degrid<S, T>(tab_off, gtab, h, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
     __syncthreads();
   }
-  (void)L::R;
 }
 
 template <class T>
@@ -183,7 +196,7 @@ __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
     const int64_t tile = bin - (int64_t)p * a.g.ntiles;
     const int ty = (int)(tile / a.g.ntx), tx = (int)(tile - (int64_t)ty * a.g.ntx);
     const int s = a.g.supp[p];
-    const int sub_off = tab_off + a.g.os * a.g.os * lay_class_bytes(s, TabElem<T>::E);
+    const int sub_off = tab_off + lay_staged_bytes(a.g.os, s, TabElem<T>::E);
     const int rec_off = sub_off + sub_bytes(a.g.tile_x, a.g.tile_y, a.group_tiles, s);
     const int cap = (a.smem_bytes - rec_off) / (int)sizeof(Record);
     int ntiles = 1;
@@ -199,7 +212,10 @@ __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
     break;
       WP_SEG_CASE(1) WP_SEG_CASE(2) WP_SEG_CASE(3) WP_SEG_CASE(4) WP_SEG_CASE(5) WP_SEG_CASE(6) WP_SEG_CASE(7)
       WP_SEG_CASE(8) WP_SEG_CASE(9) WP_SEG_CASE(10) WP_SEG_CASE(11) WP_SEG_CASE(12) WP_SEG_CASE(13)
-      WP_SEG_CASE(14) WP_SEG_CASE(15) WP_SEG_CASE(16)
+      WP_SEG_CASE(14) WP_SEG_CASE(15) WP_SEG_CASE(16) WP_SEG_CASE(17) WP_SEG_CASE(18) WP_SEG_CASE(19)
+      WP_SEG_CASE(20) WP_SEG_CASE(21) WP_SEG_CASE(22) WP_SEG_CASE(23) WP_SEG_CASE(24) WP_SEG_CASE(25)
+      WP_SEG_CASE(26) WP_SEG_CASE(27) WP_SEG_CASE(28) WP_SEG_CASE(29) WP_SEG_CASE(30) WP_SEG_CASE(31)
+      WP_SEG_CASE(32)
 #undef WP_SEG_CASE
       default:
         break;
@@ -221,6 +237,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_degrid_v2(D2Args a) {
 size_t degrid_v2_smem(const wp_ctx* ctx, int* group_tiles) {
   const int smax = *std::max_element(ctx->supp.begin(), ctx->supp.end());
   if (smax > kMaxS) return 0;
+  if (smax > kMaxStagedS && !ctx->d_lanetab) return 0;
   const int e = ctx->prm.table_type == WP_TABLE_F32 ? 4 : 2;
   const int os = ctx->prm.oversample;
   const int tx = ctx->geo.tile_x, ty = ctx->geo.tile_y;
@@ -234,7 +251,7 @@ size_t degrid_v2_smem(const wp_ctx* ctx, int* group_tiles) {
   for (; group >= 1; --group) {
     bool fits = true;
     for (int sp : ctx->supp) {
-      const size_t need = (size_t)kCountsBytes + (size_t)os * os * lay_class_bytes(sp, e) +
+      const size_t need = (size_t)kCountsBytes + (size_t)lay_staged_bytes(os, sp, e) +
                           (size_t)sub_bytes(tx, ty, group, sp) + (size_t)kMinChunk * sizeof(Record);
       if (need > bytes) fits = false;
     }
@@ -259,6 +276,8 @@ cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* out, const
   a.g = ctx->geo;
   a.tab = ctx->d_tab;
   a.tab_off = ctx->d_tab_off;
+  a.lanetab = (const unsigned char*)ctx->d_lanetab;
+  a.lanetab_off = ctx->d_lanetab_off;
   a.grid = grid;
   a.out = out;
   a.index = index;

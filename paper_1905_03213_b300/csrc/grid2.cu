@@ -41,6 +41,8 @@ struct G2Args {
   Geometry g;
   const void* tab;          // stored tables (f32, f16 or bf16 taps), layout [plane][oy*os+ox][a][b]
   const int64_t* tab_off;
+  const unsigned char* lanetab;   // lane-order tables of the planes with S > 16 (global)
+  const int64_t* lanetab_off;     // [Nw] byte offset of each plane in lanetab (-1: none)
   float2* grid;
   int smem_bytes;           // dynamic shared memory of the launch
   int group_tiles;          // origin tiles of one tile row sorted as one segment, at most
@@ -89,17 +91,19 @@ struct Footprint {
 };
 
 // One warp grids the decoded, sorted records [beg, end) of the chunk at byte offset rec_off.
-// Staged table (byte offset tab_off): per class, Lay<S, T>::CB bytes as described at Lay.
+// Table: staged in shared memory at byte offset tab_off, or (S > 16) the plane's lane-order
+// copy at gtab; per class Lay<S, T>::CB bytes as described at Lay. Row half h (S > 16).
 // Decoded record: x, y = c (float bits); z = i0 | j0 << 16; w = class byte offset | conj << 31.
 // Taps are widened to float32; every product and sum is float32.
 template <int S, class T>
-__device__ __forceinline__ void warp_grid(int tab_off, int rec_off, int beg, int end, float2* __restrict__ grid, int n) {
-  using L = Lay<S>;
+__device__ __forceinline__ void warp_grid(int tab_off, const unsigned char* gtab, int h, int rec_off, int beg,
+                                          int end, float2* __restrict__ grid, int n) {
+  using L = Lay<S, T>;
   const int lane = threadIdx.x & 31;
   const int g = lane / S, a = lane - g * S;
   const bool active = lane < L::NL;
-  const int row0 = g * L::R;
-  const unsigned char* tab = dyn_smem() + tab_off;
+  const int row0 = L::kGlobalTable ? h * L::R : g * L::R;
+  const unsigned char* tab = L::kGlobalTable ? gtab + h * L::HB : dyn_smem() + tab_off;
   const uint4* drec = (const uint4*)(dyn_smem() + rec_off);
   Footprint<S> fp;
   fp.zero();
@@ -154,14 +158,20 @@ __device__ __forceinline__ void warp_grid(int tab_off, int rec_off, int beg, int
 template <int S, class T>
 __device__ __noinline__ void grid_segment(const G2Args& a, int p, bool stage, int x0, int y0, int width, uint32_t s0,
                                           uint32_t s1, int cap, int tab_off, int rec_off) {
-  if (stage) stage_table<S, T>((const T*)a.tab + a.tab_off[p], a.g.os, tab_off);
+  using L = Lay<S, T>;
+  if constexpr (!L::kGlobalTable) {
+    if (stage) stage_table<S, T>((const T*)a.tab + a.tab_off[p], a.g.os, tab_off);
+  }
+  const unsigned char* gtab = L::kGlobalTable ? a.lanetab + a.lanetab_off[p] : nullptr;
   const int keys = width * a.g.tile_y;
   const int warp = threadIdx.x >> 5;
+  constexpr int kPieces = kWarps / L::H;            // warps of a row-half pair share a piece
+  const int piece = warp / L::H, h = warp % L::H;
   for (uint32_t c0 = s0; c0 < s1; c0 += (uint32_t)cap) {
     const int m = (int)min((uint32_t)cap, s1 - c0);
     sort_chunk<S, T>((const uint4*)a.recs, nullptr, c0, m, x0, y0, width, keys, a.g.os, rec_off);
-    const int beg = (int)((int64_t)m * warp / kWarps), end = (int)((int64_t)m * (warp + 1) / kWarps);
-    warp_grid<S, T>(tab_off, rec_off, beg, end, a.grid, a.g.n);
+    const int beg = (int)((int64_t)m * piece / kPieces), end = (int)((int64_t)m * (piece + 1) / kPieces);
+    warp_grid<S, T>(tab_off, gtab, h, rec_off, beg, end, a.grid, a.g.n);
     __syncthreads();
   }
 }
@@ -179,7 +189,7 @@ __device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end) {
     const int64_t tile = bin - (int64_t)p * a.g.ntiles;
     const int ty = (int)(tile / a.g.ntx), tx = (int)(tile - (int64_t)ty * a.g.ntx);
     const int s = a.g.supp[p];
-    const int rec_off = tab_off + a.g.os * a.g.os * lay_class_bytes(s, TabElem<T>::E);
+    const int rec_off = tab_off + lay_staged_bytes(a.g.os, s, TabElem<T>::E);
     const int cap = (a.smem_bytes - rec_off) / (int)sizeof(Record);
     int ntiles = 1;
     const uint32_t seg_end = segment_end(a.offsets, a.nbins, bin, tx, a.g.ntx, pos, end, cap, a.group_tiles, &ntiles);
@@ -194,7 +204,10 @@ __device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end) {
     break;
       WP_SEG_CASE(1) WP_SEG_CASE(2) WP_SEG_CASE(3) WP_SEG_CASE(4) WP_SEG_CASE(5) WP_SEG_CASE(6) WP_SEG_CASE(7)
       WP_SEG_CASE(8) WP_SEG_CASE(9) WP_SEG_CASE(10) WP_SEG_CASE(11) WP_SEG_CASE(12) WP_SEG_CASE(13)
-      WP_SEG_CASE(14) WP_SEG_CASE(15) WP_SEG_CASE(16)
+      WP_SEG_CASE(14) WP_SEG_CASE(15) WP_SEG_CASE(16) WP_SEG_CASE(17) WP_SEG_CASE(18) WP_SEG_CASE(19)
+      WP_SEG_CASE(20) WP_SEG_CASE(21) WP_SEG_CASE(22) WP_SEG_CASE(23) WP_SEG_CASE(24) WP_SEG_CASE(25)
+      WP_SEG_CASE(26) WP_SEG_CASE(27) WP_SEG_CASE(28) WP_SEG_CASE(29) WP_SEG_CASE(30) WP_SEG_CASE(31)
+      WP_SEG_CASE(32)
 #undef WP_SEG_CASE
       default:
         break;
@@ -207,6 +220,40 @@ template <class T>
 __global__ void __launch_bounds__(kThreads, 1) k_grid_v2(G2Args a) {
   for_each_unit(a.offsets, a.costoff, a.nbins, a.nunits, a.work,
                 [&](uint32_t beg, uint32_t end) { grid_range<T>(a, beg, end); });
+}
+
+// ---- lane-order tables in global memory for the planes with S > 16 ----
+
+// Writes plane tables (stored layout [oy*os+ox][a][b] of T) in the lane order of Lay<S> with
+// two row halves, for a runtime support s (17 .. 32); grid-stride over the table's entries.
+template <class T>
+__global__ void k_lane_table(const T* __restrict__ src, int s, int os, unsigned char* __restrict__ dst) {
+  constexpr int E = TabElem<T>::E, PB = 128 * E;
+  const int r = (s + 1) / 2, rp = r / 2, per = rp + (r & 1);
+  const int hb = lay_half_bytes(s, E), cb = 2 * hb;
+  const int n = os * os * 2 * 32 * per;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int cls = i / (2 * 32 * per), rem = i - cls * (2 * 32 * per);
+    const int h = rem / (32 * per), rem2 = rem - h * (32 * per);
+    const int k = rem2 >> 5, lane = rem2 & 31;
+    const bool active = lane < s;
+    const int b0 = h * r + 2 * k;
+    const T* col = src + ((int64_t)cls * s + lane) * s;
+    const float2 v0 = (active && b0 < s) ? tap_float2(col[b0]) : make_float2(0.f, 0.f);
+    unsigned char* base = dst + (int64_t)cls * cb + h * hb + k * PB;
+    if (k < rp) {
+      const float2 v1 = (active && b0 + 1 < s) ? tap_float2(col[b0 + 1]) : make_float2(0.f, 0.f);
+      if constexpr (E == 4) {
+        *(float2*)(base + lane * 8) = make_float2(v0.x, v1.x);
+        *(float2*)(base + 256 + lane * 8) = make_float2(v0.y, v1.y);
+      } else {
+        *(uint2*)(base + lane * 8) = make_uint2(pack_pair(T{}, v0.x, v1.x), pack_pair(T{}, v0.y, v1.y));
+      }
+    } else {
+      if constexpr (E == 4) *(float2*)(base + lane * 8) = v0;
+      else *(uint32_t*)(base + lane * 4) = pack_pair(T{}, v0.x, v0.y);
+    }
+  }
 }
 
 // ---- many jobs in one persistent launch (wp_batch_grid) ----
@@ -291,7 +338,8 @@ size_t grid_v2_smem(const wp_ctx* ctx, int* group_tiles) {
     return 0;
   const size_t bytes = (size_t)optin - 1024;        // room for the static scan scratch
   size_t tab = 0;
-  for (int sp : ctx->supp) tab = std::max(tab, (size_t)os * os * lay_class_bytes(sp, e));
+  for (int sp : ctx->supp) tab = std::max(tab, (size_t)lay_staged_bytes(os, sp, e));
+  if (smax > kMaxStagedS && !ctx->d_lanetab) return 0;
   if ((size_t)kCountsBytes + tab + (size_t)kMinChunk * sizeof(Record) > bytes) return 0;
   *group_tiles = std::max(1, std::min(8, kMaxKeys / (tx * ty)));
   return bytes;
@@ -310,6 +358,8 @@ cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used
   a.g = ctx->geo;
   a.tab = ctx->d_tab;
   a.tab_off = ctx->d_tab_off;
+  a.lanetab = (const unsigned char*)ctx->d_lanetab;
+  a.lanetab_off = ctx->d_lanetab_off;
   a.grid = grid;
   a.smem_bytes = (int)smem;
   a.group_tiles = group;
@@ -349,6 +399,8 @@ void grid_job_desc(wp_ctx* ctx, float2* grid, size_t smem, void* out) {
   a.g = ctx->geo;
   a.tab = ctx->d_tab;
   a.tab_off = ctx->d_tab_off;
+  a.lanetab = (const unsigned char*)ctx->d_lanetab;
+  a.lanetab_off = ctx->d_lanetab_off;
   a.grid = grid;
   a.smem_bytes = (int)smem;
   a.group_tiles = group;
@@ -382,6 +434,43 @@ cudaError_t launch_grid_batch(const void* d_jobs, int njobs, uint64_t* d_jobcost
     default: k_grid_batch<float2><<<nsm, kThreads, smem, s>>>(b); break;
   }
   return cudaGetLastError();
+}
+
+}  // namespace wp
+
+namespace wp {
+
+// Bytes of the lane-order table of one plane with support s (0 when it is staged instead).
+size_t lane_table_bytes(int s, int os, int table_type) {
+  const int e = table_type == WP_TABLE_F32 ? 4 : 2;
+  return s > kMaxStagedS && s <= kMaxS ? (size_t)os * os * lay_class_bytes(s, e) : 0;
+}
+
+cudaError_t launch_lane_tables(wp_ctx* ctx, cudaStream_t s) {
+  if (!ctx->d_lanetab) return cudaSuccess;
+  const int os = ctx->prm.oversample;
+  for (int p = 0; p < ctx->prm.n_w; ++p) {
+    if (ctx->lanetab_off[p] < 0) continue;
+    const int sp = ctx->supp[p];
+    unsigned char* dst = (unsigned char*)ctx->d_lanetab + ctx->lanetab_off[p];
+    const int blocks = std::min(1024, (os * os * 2 * 32 * 16 + 255) / 256);
+    switch (ctx->prm.table_type) {
+      case WP_TABLE_F16:
+        k_lane_table<__half2><<<blocks, 256, 0, s>>>((const __half2*)ctx->d_tab + ctx->tab_off[p], sp, os, dst);
+        break;
+      case WP_TABLE_BF16:
+        k_lane_table<__nv_bfloat162><<<blocks, 256, 0, s>>>((const __nv_bfloat162*)ctx->d_tab + ctx->tab_off[p], sp,
+                                                            os, dst);
+        break;
+      default:
+        k_lane_table<float2><<<blocks, 256, 0, s>>>((const float2*)ctx->d_tab + ctx->tab_off[p], sp, os, dst);
+        break;
+    }
+    ++ctx->launches;
+    const cudaError_t e = cudaGetLastError();
+    if (e) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace wp

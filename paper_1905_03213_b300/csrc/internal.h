@@ -87,6 +87,9 @@ struct wp_ctx {
   int32_t* d_supp = nullptr;
   double* d_wplane = nullptr;
   int64_t* d_tab_off = nullptr;
+  void* d_lanetab = nullptr;           // lane-order tables of the planes with S > 16 (warp kernels)
+  std::vector<int64_t> lanetab_off;    // byte offset per plane, -1 when the plane is staged
+  int64_t* d_lanetab_off = nullptr;
   int64_t* d_tab64_off = nullptr;
   int64_t* d_quad_off = nullptr;
   double* d_nu = nullptr;
@@ -148,6 +151,9 @@ cudaError_t launch_grid(wp_ctx* ctx, float2* grid, cudaStream_t s);
 cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used);
 // shared memory the warp gridding kernel needs for ctx (0: outside its limits)
 size_t grid_v2_smem(const wp_ctx* ctx, int* group_tiles);
+// lane-order global tables of the planes with S > 16 (grid2.cu)
+size_t lane_table_bytes(int s, int os, int table_type);
+cudaError_t launch_lane_tables(wp_ctx* ctx, cudaStream_t s);
 // multi-job persistent gridding (grid2.cu): per-job descriptors, then one launch over all jobs
 size_t grid_job_desc_bytes();
 void grid_job_desc(wp_ctx* ctx, float2* grid, size_t smem, void* out);

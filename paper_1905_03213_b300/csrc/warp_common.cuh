@@ -16,7 +16,8 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kMaxS = 16;                                     // larger supports: baseline kernel
+constexpr int kMaxS = 32;                                     // larger supports: baseline kernel
+constexpr int kMaxStagedS = 16;                               // larger: table read from global memory
 constexpr int kMaxKeys = 4096;                                  // origins of one segment
 constexpr int kCountsBytes = ((kMaxKeys + 1) * 4 + 15) & ~15;  // shared-memory counters
 constexpr int kMinChunk = 512;
@@ -24,21 +25,34 @@ constexpr uint32_t kNoOrigin = 0xffffffffu;
 constexpr int kUnitsPerCta = 8;                              // work units per CTA, on average
 
 
-// Lane layout for support S: G row groups of S lanes; lane g*S + a holds rows g*R ..
-// g*R + R - 1 of footprint column a, as RP row pairs and RT (0/1) single tail row.
+// Lane layout for support S <= 16: G row groups of S lanes; lane g*S + a holds rows g*R ..
+// g*R + R - 1 of footprint column a, as RP row pairs and RT (0/1) single tail row. For
+// 16 < S <= 32 (H = 2 row halves) two warps share the records of one piece: lane a of warp
+// half h holds rows h*R .. h*R + R - 1 (R = ceil(S/2)) of column a.
 //
-// Staged table of one oversampling class, for tap components of E bytes (4: f32, 2: f16/bf16),
-// one entry per lane in 32-lane blocks (lanes beyond G*S hold zeros):
+// Table of one oversampling class in lane order, for tap components of E bytes (4: f32, 2:
+// f16/bf16), one entry per lane in 32-lane blocks (lanes and rows outside the footprint hold
+// zeros), per row half:
 //   f32:     per row pair k a block of float2 {kr(2k), kr(2k+1)} then a block of float2
 //            {ki(2k), ki(2k+1)}; then for the tail row a block of float2 {kr, ki}.
 //   f16/bf16: per row pair k one block of 8-byte entries {kr(2k), kr(2k+1), ki(2k), ki(2k+1)};
 //            then for the tail row a block of 4-byte entries {kr, ki}.
-// Either way a lane reads 8 bytes per row pair and load instruction.
-__host__ __device__ constexpr int lay_rows(int s) { return (s + 32 / s - 1) / (32 / s); }
-__host__ __device__ constexpr int lay_groups(int s) { return (s + lay_rows(s) - 1) / lay_rows(s); }
-// staged bytes per oversampling class
-__host__ __device__ constexpr int lay_class_bytes(int s, int e) {
+// Either way a lane reads 8 bytes per row pair and load instruction. Tables of S <= 16 are
+// staged in shared memory per plane; for S > 16 a copy in this layout is built in global memory
+// once (it does not fit shared memory at oversampling 8) and read through the L1/L2 path.
+__host__ __device__ constexpr int lay_halves(int s) { return s > kMaxStagedS ? 2 : 1; }
+__host__ __device__ constexpr int lay_rows(int s) { return s > kMaxStagedS ? (s + 1) / 2 : (s + 32 / s - 1) / (32 / s); }
+__host__ __device__ constexpr int lay_groups(int s) { return s > kMaxStagedS ? 1 : (s + lay_rows(s) - 1) / lay_rows(s); }
+// rows spanned by the lanes of all groups or halves (>= s)
+__host__ __device__ constexpr int lay_span(int s) { return lay_rows(s) * (lay_groups(s) > lay_halves(s) ? lay_groups(s) : lay_halves(s)); }
+// bytes of one row half of a class, and of a class
+__host__ __device__ constexpr int lay_half_bytes(int s, int e) {
   return ((lay_rows(s) / 2) * 128 + (lay_rows(s) & 1) * 64) * e;
+}
+__host__ __device__ constexpr int lay_class_bytes(int s, int e) { return lay_halves(s) * lay_half_bytes(s, e); }
+// bytes of one plane's table in shared memory (0: read from global memory)
+__host__ __device__ constexpr int lay_staged_bytes(int os, int s, int e) {
+  return s > kMaxStagedS ? 0 : os * os * lay_class_bytes(s, e);
 }
 
 template <class T>
@@ -58,11 +72,13 @@ struct TabElem<__nv_bfloat162> {
 
 template <int S, class T = float2>
 struct Lay {
-  static constexpr int R = lay_rows(S), G = lay_groups(S), NL = G * S;
+  static constexpr int R = lay_rows(S), G = lay_groups(S), H = lay_halves(S), NL = G * S;
   static constexpr int RP = R / 2, RT = R & 1, RPA = RP > 0 ? RP : 1;
   static constexpr int E = TabElem<T>::E;
   static constexpr int PB = 128 * E;           // bytes of one row pair's blocks
+  static constexpr int HB = lay_half_bytes(S, E);
   static constexpr int CB = lay_class_bytes(S, E);
+  static constexpr bool kGlobalTable = H > 1;
 };
 
 __device__ __forceinline__ unsigned char* dyn_smem() {
@@ -174,30 +190,36 @@ template <int S, class T = float2>
 struct Taps {
   unsigned long long r[Lay<S, T>::RPA], i[Lay<S, T>::RPA];
   float tr, ti;
-  // Lanes beyond the layout (lane >= NL) read their all-zero table entries.
+  // Lanes beyond the layout (lane >= NL) read their all-zero table entries. cls_base points into
+  // shared memory, or (kGlobalTable) into the global copy, read through the read-only path.
+  template <class U>
+  static __device__ __forceinline__ U rd(const unsigned char* p) {
+    if constexpr (Lay<S, T>::kGlobalTable) return __ldg((const U*)p);
+    else return *(const U*)p;
+  }
   __device__ __forceinline__ void load(const unsigned char* cls_base, int lane) {
     using L = Lay<S, T>;
     if constexpr (L::E == 4) {
 #pragma unroll
       for (int k = 0; k < L::RP; ++k) {
-        r[k] = *(const unsigned long long*)(cls_base + k * L::PB + lane * 8);
-        i[k] = *(const unsigned long long*)(cls_base + k * L::PB + 256 + lane * 8);
+        r[k] = rd<unsigned long long>(cls_base + k * L::PB + lane * 8);
+        i[k] = rd<unsigned long long>(cls_base + k * L::PB + 256 + lane * 8);
       }
       if (L::RT) {
-        const float2 t = *(const float2*)(cls_base + L::RP * L::PB + lane * 8);
+        const float2 t = rd<float2>(cls_base + L::RP * L::PB + lane * 8);
         tr = t.x;
         ti = t.y;
       }
     } else {
 #pragma unroll
       for (int k = 0; k < L::RP; ++k) {
-        const uint2 v = *(const uint2*)(cls_base + k * L::PB + lane * 8);
+        const uint2 v = rd<uint2>(cls_base + k * L::PB + lane * 8);
         const float2 a = to_float2(bits_as<T>(v.x)), b = to_float2(bits_as<T>(v.y));
         r[k] = pack2(a.x, a.y);
         i[k] = pack2(b.x, b.y);
       }
       if (L::RT) {
-        const float2 t = to_float2(bits_as<T>(*(const uint32_t*)(cls_base + L::RP * L::PB + lane * 4)));
+        const float2 t = to_float2(bits_as<T>(rd<uint32_t>(cls_base + L::RP * L::PB + lane * 4)));
         tr = t.x;
         ti = t.y;
       }

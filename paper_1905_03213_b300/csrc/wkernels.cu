@@ -223,7 +223,10 @@ cudaError_t launch_make_wkernels(wp_ctx* ctx, cudaStream_t s) {
       k_tables<float2><<<nblk(total, 256), 256, 0, s>>>(kg, ctx->d_quad, ctx->d_nu, ctx->d_tab64_off, ctx->d_tab64,
                                                         (float2*)ctx->d_tab, total);
   }
-  return cudaGetLastError();
+  const cudaError_t et = cudaGetLastError();
+  if (et) return et;
+  // lane-order copies of the planes with S > 16 for the warp kernels
+  return launch_lane_tables(ctx, s);
 }
 
 }  // namespace wp

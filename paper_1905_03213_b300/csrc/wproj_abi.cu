@@ -190,7 +190,7 @@ void wp_destroy(wp_ctx* ctx) {
                   ctx->d_stage,    ctx->d_quad,      ctx->d_tab64,     ctx->d_tab,      ctx->d_supp,
                   ctx->d_wplane,   ctx->d_tab_off,   ctx->d_tab64_off, ctx->d_quad_off, ctx->d_nu,
                   ctx->d_counts,   ctx->d_offsets,   ctx->d_cursor,    ctx->d_partials, ctx->d_chan,
-                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2, ctx->d_work, ctx->rounded.ptr, ctx->rec_index.ptr, ctx->d_suboff};
+                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2, ctx->d_work, ctx->rounded.ptr, ctx->rec_index.ptr, ctx->d_suboff, ctx->d_lanetab, ctx->d_lanetab_off};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -266,6 +266,12 @@ int wp_create(wp_ctx** out, const wp_params* p) {
   }
   ctx->tab_elems = acc;
   ctx->tab64_elems = acc;
+  int64_t lane_bytes = 0;                 // lane-order tables of the planes with S > 16
+  for (int i = 0; i < q.n_w; ++i) {
+    const size_t b = wp::lane_table_bytes(ctx->supp[i], q.oversample, q.table_type);
+    ctx->lanetab_off.push_back(b ? lane_bytes : -1);
+    lane_bytes += (int64_t)((b + 255) & ~(size_t)255);
+  }
   ctx->quad_elems = accq;
   ctx->taper_c = M_PI * q.support_min / 2.0;
   ctx->legendre = wp::pswf_legendre_coefficients(ctx->taper_c);
@@ -293,7 +299,11 @@ int wp_create(wp_ctx** out, const wp_params* p) {
   int dmax = 0;
   for (int i = 0; i < q.n_w; ++i) dmax = std::max(dmax, ctx->supp[i] * q.oversample / 2 + 1);
   const size_t tab_bytes = (q.table_type == WP_TABLE_F32 ? 8 : 4) * (size_t)ctx->tab_elems;
-  bool ok = dalloc(&ctx->d_legendre, ctx->legendre.size()) == cudaSuccess &&
+  bool ok = (lane_bytes == 0 || (cudaMalloc(&ctx->d_lanetab, (size_t)lane_bytes) == cudaSuccess &&
+                                  dalloc(&ctx->d_lanetab_off, (size_t)q.n_w) == cudaSuccess &&
+                                  cudaMemcpy(ctx->d_lanetab_off, ctx->lanetab_off.data(), sizeof(int64_t) * q.n_w,
+                                             cudaMemcpyHostToDevice) == cudaSuccess)) &&
+            dalloc(&ctx->d_legendre, ctx->legendre.size()) == cudaSuccess &&
             dalloc(&ctx->d_taper_img, (size_t)q.n) == cudaSuccess && dalloc(&ctx->d_taper_inv, (size_t)q.n) == cudaSuccess && dalloc(&ctx->d_taper_lat, (size_t)h) == cudaSuccess &&
             dalloc(&ctx->d_cos, (size_t)q.oversample * ctx->m) == cudaSuccess &&
             dalloc(&ctx->d_screen, (size_t)q.n_w * h * h) == cudaSuccess &&

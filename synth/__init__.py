@@ -269,3 +269,56 @@ def random_grid(n: int, seed: int) -> np.ndarray:
     """Unit-variance complex64 [n, n] grid (degridding parity input)."""
     rng = np.random.default_rng(seed)
     return (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).astype(np.complex64)
+
+
+# ---------------------------------------------------------------- batched imaging jobs
+
+@dataclass
+class JobSpec:
+    """One imaging job of the batched workload: its array, grid and kernel geometry."""
+    n: int
+    n_w: int
+    s_min: int
+    s_max: int
+    oversample: int
+    n_ant: int
+    n_time: int
+    freqs: np.ndarray
+    cell: float
+    radius_m: float
+    seed: int
+
+
+def batch_jobs(n_jobs: int = 64, seed: int = 1004, nvis_min: float = 1e4, nvis_max: float = 2e7,
+               scale: float = 1.0) -> list[JobSpec]:
+    """Channel / snapshot imaging jobs of uneven sizes: grid sizes from {512, 1024, 2048, 4096},
+    visibility counts log-uniform in [nvis_min, nvis_max] (times `scale`), supports 7-31,
+    oversampling 4-8 and 8-64 w-planes. Snapshot jobs have many baselines and few samples,
+    channel jobs one channel and long tracks; the cell size makes the longest baseline fill the
+    grid to 95%."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for j in range(n_jobs):
+        n = int(rng.choice([512, 1024, 2048, 4096]))
+        nvis = float(np.exp(rng.uniform(np.log(nvis_min), np.log(nvis_max)))) * scale
+        s_min = int(rng.integers(7, 32))
+        s_max = int(rng.integers(s_min, 32))
+        os_ = int(rng.integers(4, 9))
+        n_w = int(rng.integers(8, 65))
+        nchan = int(rng.choice([1, 2, 4]))
+        n_ant = int(rng.integers(16, 129))
+        nbl = n_ant * (n_ant - 1) // 2
+        n_time = max(1, int(round(nvis / (nbl * nchan))))
+        radius = float(rng.uniform(1000.0, 8000.0))
+        freqs = np.linspace(1.0e9, 1.4e9, nchan) if nchan > 1 else np.array([1.2e9])
+        umax = 2.0 * radius * freqs.max() / C_LIGHT           # longest baseline in wavelengths
+        cell = 1.0 / (2.0 * umax / 0.95)
+        jobs.append(JobSpec(n, n_w, s_min, s_max, os_, n_ant, n_time, freqs, cell, radius, seed * 100 + j))
+    return jobs
+
+
+def job_uvw(spec: JobSpec) -> np.ndarray:
+    """uvw [n_baselines * n_time, 3] (m) of a job's array over 6 h at declination +40 deg."""
+    rng = np.random.default_rng(spec.seed)
+    enu = antenna_enu(spec.n_ant, spec.radius_m, 20.0, rng)
+    return uvw_metres(enu, SITE_LAT, 40 * DEG, hour_angles(spec.n_time, 6.0))

@@ -133,6 +133,35 @@ def test_grid_tile_shapes(torch_cuda, tile):
     assert eg < 1e-6, (tile, eg)
 
 
+@pytest.mark.parametrize("table,pairs,os_", [("f32", False, 8), ("f32", True, 4), ("f16", False, 8), ("bf16", True, 6)])
+def test_grid_and_degrid_large_supports(torch_cuda, table, pairs, os_):
+    """Supports 7-30: planes above 16 run with two row halves per piece and lane-order tables
+    read from global memory, planes up to 16 with staged tables, in the same launch. (The taper
+    follows S_min: with a larger S_min it is so small at the inner half's edge that the
+    taper-corrected image magnifies f16 table rounding past 1e-3 there, table or no table.)"""
+    import torch
+    case = random_case(n=128, nrow=1200, nchan=2, n_w=7, s_min=7, s_max=30, os_=os_, pairs=pairs, seed=41)
+    crd, g_ref, sw_ref = oracle_results(case)
+    g, img, raw, sw, nd = _grid_and_image(case, table=table)
+    eg, _ = peak_rel(g, g_ref)
+    assert eg < (1e-6 if table == "f32" else TOL_IMAGE[table]), eg
+    emax, detail = _image_errors(case, g_ref, sw_ref, img, raw)
+    if table == "f32":
+        assert emax < TOL_IMAGE["f32"], detail
+    else:
+        # 16-bit tables: the mixed-precision bound on the dirty image (uncorrected, all pixels);
+        # the taper-corrected inner half magnifies the table rounding by up to 1/(t t) there
+        assert detail[0] < 1e-3 and detail[2] < 5e-3, detail
+    crd1 = oracle.coords(case.uvw, case.freqs, case.prm)
+    gh = synth.random_grid(case.prm.n, 17)
+    ref = oracle.degrid(crd1, gh.astype(np.complex128), case.tables, case.prm).reshape(case.vis.shape)
+    wp = make_wproj(case, table=table)
+    uvw, f, _, _ = to_dev(case)
+    out = wp.degrid(uvw, f, torch.from_numpy(gh).cuda()).cpu().numpy()
+    e, _ = peak_rel(out, ref)
+    assert e < TOL_IMAGE[table], e
+
+
 @pytest.mark.parametrize("table", ["f16", "bf16"])
 def test_grid_reduced_precision_tables(torch_cuda, table):
     case = parity_case()
