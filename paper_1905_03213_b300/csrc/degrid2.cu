@@ -79,7 +79,7 @@ __device__ __forceinline__ void batch_reduce(float (&v)[NB], int lane) {
 // from the grid region staged at sub_off (pitch entries per row, origin (sx0, sy0)). Table as
 // in the gridding kernel (staged at tab_off, or the global copy gtab for S > 16, row half h);
 // with two row halves each warp adds its half of every visibility to the (zeroed) output.
-template <int S, class T>
+template <int S, class T, bool kGlobal>
 __device__ __forceinline__ void warp_degrid(int tab_off, const unsigned char* gtab, int h, int sub_off, int pitch,
                                             int sx0, int sy0, int rec_off, int beg, int end,
                                             float2* __restrict__ out) {
@@ -88,8 +88,8 @@ __device__ __forceinline__ void warp_degrid(int tab_off, const unsigned char* gt
   const int lane = threadIdx.x & 31;
   const int g = lane / S, a = lane - g * S;
   // lanes beyond the layout read (zero-tap) cells of the half's first row
-  const int row0 = L::kGlobalTable ? h * L::R : (lane < L::NL ? g * L::R : 0);
-  const unsigned char* tab = L::kGlobalTable ? gtab + h * L::HB : dyn_smem() + tab_off;
+  const int row0 = L::H > 1 ? h * L::R : (lane < L::NL ? g * L::R : 0);
+  const unsigned char* tab = (kGlobal ? gtab : dyn_smem() + tab_off) + h * L::HB;
   const float2* sub = (const float2*)(dyn_smem() + sub_off);
   const uint4* drec = (const uint4*)(dyn_smem() + rec_off);
   unsigned long long GR[L::RPA], GI[L::RPA], NGI[L::RPA];   // cells: re, im, -im of row pairs
@@ -104,7 +104,7 @@ __device__ __forceinline__ void warp_degrid(int tab_off, const unsigned char* gt
       pre[r] = pim[r] = 0.f;
       if (b0 + r < end) {                          // warp-uniform
         const uint4 rec = drec[b0 + r];
-        Taps<S, T> tv;
+        Taps<S, T, kGlobal> tv;
         tv.load(tab + (rec.w & 0x7fffffffu), lane);
         if (rec.z != cz) {                         // warp-uniform: load the cells under the new origin
           cz = rec.z;
@@ -155,14 +155,12 @@ __device__ __forceinline__ void warp_degrid(int tab_off, const unsigned char* gt
 }
 
 template <int S, class T>
-__device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, int x0, int y0, int width,
+__device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, bool staged, int x0, int y0, int width,
                                             uint32_t s0, uint32_t s1, int cap, int tab_off, int sub_off,
                                             int rec_off) {
   using L = Lay<S, T>;
-  if constexpr (!L::kGlobalTable) {
-    if (stage) stage_table<S, T>((const T*)a.tab + a.tab_off[p], a.g.os, tab_off);
-  }
-  const unsigned char* gtab = L::kGlobalTable ? a.lanetab + a.lanetab_off[p] : nullptr;
+  if (staged && stage) stage_table<S, T>((const T*)a.tab + a.tab_off[p], a.g.os, tab_off);
+  const unsigned char* gtab = staged ? nullptr : a.lanetab + a.lanetab_off[p];
   constexpr int kPieces = kWarps / L::H;            // warps of a row-half pair share a piece
   // the grid region under the segment's footprints (cells outside the grid read as zero)
   const int cols = width + S - 1, rows = sub_rows(a.g.tile_y, S), pitch = sub_pitch(cols);
@@ -179,7 +177,8 @@ __device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, 
     const int kept = sort_chunk<S, T>((const uint4*)a.recs, a.index, c0, m, x0, y0, width, keys, a.g.os, rec_off);
     const int piece = warp / L::H, h = warp % L::H;
     const int beg = (int)((int64_t)kept * piece / kPieces), end = (int)((int64_t)kept * (piece + 1) / kPieces);
-    warp_degrid<S, T>(tab_off, gtab, h, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
+    if (L::H == 1 || staged) warp_degrid<S, T, false>(tab_off, nullptr, h, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
+    else warp_degrid<S, T, true>(tab_off, gtab, h, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
     __syncthreads();
   }
 }
@@ -196,19 +195,23 @@ __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
     const int64_t tile = bin - (int64_t)p * a.g.ntiles;
     const int ty = (int)(tile / a.g.ntx), tx = (int)(tile - (int64_t)ty * a.g.ntx);
     const int s = a.g.supp[p];
-    const int sub_off = tab_off + lay_staged_bytes(a.g.os, s, TabElem<T>::E);
-    const int rec_off = sub_off + sub_bytes(a.g.tile_x, a.g.tile_y, a.group_tiles, s);
+    // tables of S > 16 are staged too when they leave room for the grid region and a chunk
+    const int tbytes = a.g.os * a.g.os * lay_class_bytes(s, TabElem<T>::E);
+    const int sbytes = sub_bytes(a.g.tile_x, a.g.tile_y, a.group_tiles, s);
+    const bool staged = s <= kMaxStagedS || tab_off + tbytes + sbytes + kStagedChunk * (int)sizeof(Record) <= a.smem_bytes;
+    const int sub_off = tab_off + (staged ? tbytes : 0);
+    const int rec_off = sub_off + sbytes;
     const int cap = (a.smem_bytes - rec_off) / (int)sizeof(Record);
     int ntiles = 1;
     const uint32_t seg_end = segment_end(a.offsets, a.nbins, bin, tx, a.g.ntx, pos, end, cap, a.group_tiles, &ntiles);
-    const bool stage = p != cur_plane;
-    cur_plane = p;
+    const bool stage = staged && p != cur_plane;
+    cur_plane = staged ? p : -1;                  // an unstaged segment's grid region overwrites the table
     const int x0 = tx * a.g.tile_x, y0 = ty * a.g.tile_y;
     const int width = ntiles * a.g.tile_x;
     switch (s) {
 #define WP_SEG_CASE(N)                                                                                   \
   case N:                                                                                                \
-    degrid_segment<N, T>(a, p, stage, x0, y0, width, pos, seg_end, cap, tab_off, sub_off, rec_off);         \
+    degrid_segment<N, T>(a, p, stage, staged, x0, y0, width, pos, seg_end, cap, tab_off, sub_off, rec_off); \
     break;
       WP_SEG_CASE(1) WP_SEG_CASE(2) WP_SEG_CASE(3) WP_SEG_CASE(4) WP_SEG_CASE(5) WP_SEG_CASE(6) WP_SEG_CASE(7)
       WP_SEG_CASE(8) WP_SEG_CASE(9) WP_SEG_CASE(10) WP_SEG_CASE(11) WP_SEG_CASE(12) WP_SEG_CASE(13)

@@ -91,19 +91,20 @@ struct Footprint {
 };
 
 // One warp grids the decoded, sorted records [beg, end) of the chunk at byte offset rec_off.
-// Table: staged in shared memory at byte offset tab_off, or (S > 16) the plane's lane-order
-// copy at gtab; per class Lay<S, T>::CB bytes as described at Lay. Row half h (S > 16).
+// Table: staged in shared memory at byte offset tab_off, or (kGlobal: S > 16 and too large to
+// stage beside a chunk) the plane's lane-order copy at gtab; per class Lay<S, T>::CB bytes as
+// described at Lay. Row half h (S > 16).
 // Decoded record: x, y = c (float bits); z = i0 | j0 << 16; w = class byte offset | conj << 31.
 // Taps are widened to float32; every product and sum is float32.
-template <int S, class T>
+template <int S, class T, bool kGlobal>
 __device__ __forceinline__ void warp_grid(int tab_off, const unsigned char* gtab, int h, int rec_off, int beg,
                                           int end, float2* __restrict__ grid, int n) {
   using L = Lay<S, T>;
   const int lane = threadIdx.x & 31;
   const int g = lane / S, a = lane - g * S;
   const bool active = lane < L::NL;
-  const int row0 = L::kGlobalTable ? h * L::R : g * L::R;
-  const unsigned char* tab = L::kGlobalTable ? gtab + h * L::HB : dyn_smem() + tab_off;
+  const int row0 = L::H > 1 ? h * L::R : g * L::R;
+  const unsigned char* tab = (kGlobal ? gtab : dyn_smem() + tab_off) + h * L::HB;
   const uint4* drec = (const uint4*)(dyn_smem() + rec_off);
   Footprint<S> fp;
   fp.zero();
@@ -112,7 +113,7 @@ __device__ __forceinline__ void warp_grid(int tab_off, const unsigned char* gtab
 #pragma unroll(L::RP > 1 ? 2 : 4)
   for (int q = beg; q < end; ++q) {
     const uint4 rec = drec[q];
-    Taps<S, T> tv;
+    Taps<S, T, kGlobal> tv;
     tv.load(tab + (rec.w & 0x7fffffffu), lane);
     if (rec.z != cz) {                             // warp-uniform: a new footprint origin
       const int i0 = rec.z & 0xffff, j0 = rec.z >> 16;
@@ -156,13 +157,11 @@ __device__ __forceinline__ void warp_grid(int tab_off, const unsigned char* gtab
 }
 
 template <int S, class T>
-__device__ __noinline__ void grid_segment(const G2Args& a, int p, bool stage, int x0, int y0, int width, uint32_t s0,
-                                          uint32_t s1, int cap, int tab_off, int rec_off) {
+__device__ __noinline__ void grid_segment(const G2Args& a, int p, bool stage, bool staged, int x0, int y0, int width,
+                                          uint32_t s0, uint32_t s1, int cap, int tab_off, int rec_off) {
   using L = Lay<S, T>;
-  if constexpr (!L::kGlobalTable) {
-    if (stage) stage_table<S, T>((const T*)a.tab + a.tab_off[p], a.g.os, tab_off);
-  }
-  const unsigned char* gtab = L::kGlobalTable ? a.lanetab + a.lanetab_off[p] : nullptr;
+  if (staged && stage) stage_table<S, T>((const T*)a.tab + a.tab_off[p], a.g.os, tab_off);
+  const unsigned char* gtab = staged ? nullptr : a.lanetab + a.lanetab_off[p];
   const int keys = width * a.g.tile_y;
   const int warp = threadIdx.x >> 5;
   constexpr int kPieces = kWarps / L::H;            // warps of a row-half pair share a piece
@@ -171,7 +170,8 @@ __device__ __noinline__ void grid_segment(const G2Args& a, int p, bool stage, in
     const int m = (int)min((uint32_t)cap, s1 - c0);
     sort_chunk<S, T>((const uint4*)a.recs, nullptr, c0, m, x0, y0, width, keys, a.g.os, rec_off);
     const int beg = (int)((int64_t)m * piece / kPieces), end = (int)((int64_t)m * (piece + 1) / kPieces);
-    warp_grid<S, T>(tab_off, gtab, h, rec_off, beg, end, a.grid, a.g.n);
+    if (L::H == 1 || staged) warp_grid<S, T, false>(tab_off, nullptr, h, rec_off, beg, end, a.grid, a.g.n);
+    else warp_grid<S, T, true>(tab_off, gtab, h, rec_off, beg, end, a.grid, a.g.n);
     __syncthreads();
   }
 }
@@ -189,18 +189,21 @@ __device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end) {
     const int64_t tile = bin - (int64_t)p * a.g.ntiles;
     const int ty = (int)(tile / a.g.ntx), tx = (int)(tile - (int64_t)ty * a.g.ntx);
     const int s = a.g.supp[p];
-    const int rec_off = tab_off + lay_staged_bytes(a.g.os, s, TabElem<T>::E);
+    // tables of S > 16 are staged too when they leave room for a chunk of kStagedChunk records
+    const int tbytes = a.g.os * a.g.os * lay_class_bytes(s, TabElem<T>::E);
+    const bool staged = s <= kMaxStagedS || tab_off + tbytes + kStagedChunk * (int)sizeof(Record) <= a.smem_bytes;
+    const int rec_off = tab_off + (staged ? tbytes : 0);
     const int cap = (a.smem_bytes - rec_off) / (int)sizeof(Record);
     int ntiles = 1;
     const uint32_t seg_end = segment_end(a.offsets, a.nbins, bin, tx, a.g.ntx, pos, end, cap, a.group_tiles, &ntiles);
-    const bool stage = p != cur_plane;
-    cur_plane = p;
+    const bool stage = staged && p != cur_plane;
+    cur_plane = staged ? p : -1;                  // an unstaged segment's records overwrite the table
     const int x0 = tx * a.g.tile_x, y0 = ty * a.g.tile_y;
     const int width = ntiles * a.g.tile_x;
     switch (s) {
 #define WP_SEG_CASE(N)                                                                   \
   case N:                                                                                \
-    grid_segment<N, T>(a, p, stage, x0, y0, width, pos, seg_end, cap, tab_off, rec_off);    \
+    grid_segment<N, T>(a, p, stage, staged, x0, y0, width, pos, seg_end, cap, tab_off, rec_off);   \
     break;
       WP_SEG_CASE(1) WP_SEG_CASE(2) WP_SEG_CASE(3) WP_SEG_CASE(4) WP_SEG_CASE(5) WP_SEG_CASE(6) WP_SEG_CASE(7)
       WP_SEG_CASE(8) WP_SEG_CASE(9) WP_SEG_CASE(10) WP_SEG_CASE(11) WP_SEG_CASE(12) WP_SEG_CASE(13)
@@ -228,35 +231,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_v2(G2Args a) {
 // two row halves, for a runtime support s (17 .. 32); grid-stride over the table's entries.
 template <class T>
 __global__ void k_lane_table(const T* __restrict__ src, int s, int os, unsigned char* __restrict__ dst) {
-  constexpr int E = TabElem<T>::E, PB = 128 * E;
-  const int r = (s + 1) / 2, rp = r / 2, per = rp + (r & 1);
-  const int hb = lay_half_bytes(s, E), cb = 2 * hb;
-  const int n = os * os * 2 * 32 * per;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int cls = i / (2 * 32 * per), rem = i - cls * (2 * 32 * per);
-    const int h = rem / (32 * per), rem2 = rem - h * (32 * per);
-    const int k = rem2 >> 5, lane = rem2 & 31;
-    const bool active = lane < s;
-    const int b0 = h * r + 2 * k;
-    const T* col = src + ((int64_t)cls * s + lane) * s;
-    const float2 v0 = (active && b0 < s) ? tap_float2(col[b0]) : make_float2(0.f, 0.f);
-    unsigned char* base = dst + (int64_t)cls * cb + h * hb + k * PB;
-    if (k < rp) {
-      const float2 v1 = (active && b0 + 1 < s) ? tap_float2(col[b0 + 1]) : make_float2(0.f, 0.f);
-      if constexpr (E == 4) {
-        *(float2*)(base + lane * 8) = make_float2(v0.x, v1.x);
-        *(float2*)(base + 256 + lane * 8) = make_float2(v0.y, v1.y);
-      } else {
-        *(uint2*)(base + lane * 8) = make_uint2(pack_pair(T{}, v0.x, v1.x), pack_pair(T{}, v0.y, v1.y));
-      }
-    } else {
-      if constexpr (E == 4) *(float2*)(base + lane * 8) = v0;
-      else *(uint32_t*)(base + lane * 4) = pack_pair(T{}, v0.x, v0.y);
-    }
-  }
+  const int n = half_entries(os, s);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) write_half_entry<T>(src, s, dst, i);
 }
 
 // ---- many jobs in one persistent launch (wp_batch_grid) ----
+
+// Finer units than a single job uses: the units running at one time then cover a small slice of
+// the concatenated work, so the CTAs of a moment mostly share one job's grid and tables in L2.
+constexpr int kBatchUnitsPerCta = 64;
 
 struct BatchArgs {
   const G2Args* jobs;        // [njobs] per-job arguments (device), smem_bytes shared
@@ -426,7 +409,7 @@ cudaError_t launch_grid_batch(const void* d_jobs, int njobs, uint64_t* d_jobcost
   b.jobs = (const G2Args*)d_jobs;
   b.jobcost = d_jobcost;
   b.njobs = njobs;
-  b.nunits = nsm * kUnitsPerCta;
+  b.nunits = nsm * kBatchUnitsPerCta;
   b.work = d_work;
   switch (table_type) {
     case WP_TABLE_F16: k_grid_batch<__half2><<<nsm, kThreads, smem, s>>>(b); break;

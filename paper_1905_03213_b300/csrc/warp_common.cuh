@@ -17,7 +17,8 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxS = 32;                                     // larger supports: baseline kernel
-constexpr int kMaxStagedS = 16;                               // larger: table read from global memory
+constexpr int kMaxStagedS = 16;                               // larger: staged if it fits, else global
+constexpr int kStagedChunk = 2048;                            // records left room for beside a large table
 constexpr int kMaxKeys = 4096;                                  // origins of one segment
 constexpr int kCountsBytes = ((kMaxKeys + 1) * 4 + 15) & ~15;  // shared-memory counters
 constexpr int kMinChunk = 512;
@@ -50,7 +51,8 @@ __host__ __device__ constexpr int lay_half_bytes(int s, int e) {
   return ((lay_rows(s) / 2) * 128 + (lay_rows(s) & 1) * 64) * e;
 }
 __host__ __device__ constexpr int lay_class_bytes(int s, int e) { return lay_halves(s) * lay_half_bytes(s, e); }
-// bytes of one plane's table in shared memory (0: read from global memory)
+// bytes of one plane's table that must fit shared memory (S <= 16; larger tables are staged
+// only when they fit beside a chunk, else read from their global copy)
 __host__ __device__ constexpr int lay_staged_bytes(int os, int s, int e) {
   return s > kMaxStagedS ? 0 : os * os * lay_class_bytes(s, e);
 }
@@ -78,7 +80,6 @@ struct Lay {
   static constexpr int PB = 128 * E;           // bytes of one row pair's blocks
   static constexpr int HB = lay_half_bytes(S, E);
   static constexpr int CB = lay_class_bytes(S, E);
-  static constexpr bool kGlobalTable = H > 1;
 };
 
 __device__ __forceinline__ unsigned char* dyn_smem() {
@@ -186,15 +187,15 @@ __device__ __forceinline__ T bits_as(uint32_t u) {
 
 // This lane's taps of one record as float32: RP row pairs packed {kr(2k), kr(2k+1)} and
 // {ki(2k), ki(2k+1)} for f32x2 FMAs, and the tail row.
-template <int S, class T = float2>
+template <int S, class T = float2, bool kGlobal = false>
 struct Taps {
   unsigned long long r[Lay<S, T>::RPA], i[Lay<S, T>::RPA];
   float tr, ti;
   // Lanes beyond the layout (lane >= NL) read their all-zero table entries. cls_base points into
-  // shared memory, or (kGlobalTable) into the global copy, read through the read-only path.
+  // shared memory, or (kGlobal) into the global lane-order copy, read through the read-only path.
   template <class U>
   static __device__ __forceinline__ U rd(const unsigned char* p) {
-    if constexpr (Lay<S, T>::kGlobalTable) return __ldg((const U*)p);
+    if constexpr (kGlobal) return __ldg((const U*)p);
     else return *(const U*)p;
   }
   __device__ __forceinline__ void load(const unsigned char* cls_base, int lane) {
@@ -243,12 +244,48 @@ __device__ __forceinline__ uint32_t pack_pair(__nv_bfloat162, float a, float b) 
   return u;
 }
 
+// Entry i of the two-row-half lane layout (16 < s <= 32) of one plane's table: the table's
+// classes x halves x (row pairs + tail) x 32 lanes entries in order; writes it below dst.
+template <class T>
+__device__ __forceinline__ void write_half_entry(const T* __restrict__ src, int s, unsigned char* dst, int i) {
+  constexpr int E = TabElem<T>::E, PB = 128 * E;
+  const int r = (s + 1) / 2, rp = r / 2, per = rp + (r & 1);
+  const int hb = lay_half_bytes(s, E), cb = 2 * hb;
+  const int cls = i / (2 * 32 * per), rem = i - cls * (2 * 32 * per);
+  const int h = rem / (32 * per), rem2 = rem - h * (32 * per);
+  const int k = rem2 >> 5, lane = rem2 & 31;
+  const bool active = lane < s;
+  const int b0 = h * r + 2 * k;
+  const T* col = src + ((int64_t)cls * s + lane) * s;
+  const float2 v0 = (active && b0 < s) ? tap_float2(col[b0]) : make_float2(0.f, 0.f);
+  unsigned char* base = dst + (int64_t)cls * cb + h * hb + k * PB;
+  if (k < rp) {
+    const float2 v1 = (active && b0 + 1 < s) ? tap_float2(col[b0 + 1]) : make_float2(0.f, 0.f);
+    if constexpr (E == 4) {
+      *(float2*)(base + lane * 8) = make_float2(v0.x, v1.x);
+      *(float2*)(base + 256 + lane * 8) = make_float2(v0.y, v1.y);
+    } else {
+      *(uint2*)(base + lane * 8) = make_uint2(pack_pair(T{}, v0.x, v1.x), pack_pair(T{}, v0.y, v1.y));
+    }
+  } else {
+    if constexpr (E == 4) *(float2*)(base + lane * 8) = v0;
+    else *(uint32_t*)(base + lane * 4) = pack_pair(T{}, v0.x, v0.y);
+  }
+}
+__host__ __device__ constexpr int half_entries(int os, int s) {
+  return os * os * 2 * 32 * ((s + 1) / 2 / 2 + ((s + 1) / 2 & 1));
+}
+
 // Stages one plane's table (src: stored layout [oy*os+ox][a][b] of T) in the lane layout of
 // Lay<S, T> at byte offset tab_off of the dynamic shared memory. 16-bit components are copied
 // exactly (each is representable after the round trip through float32).
 template <int S, class T = float2>
 __device__ __forceinline__ void stage_table(const T* __restrict__ src, int os, int tab_off) {
   using L = Lay<S, T>;
+  if constexpr (L::H > 1) {
+    for (int i = threadIdx.x; i < half_entries(os, S); i += kThreads) write_half_entry<T>(src, S, dyn_smem() + tab_off, i);
+    return;
+  }
   constexpr int kPer = L::RP + L::RT;           // entries per lane and class
   const int ncls = os * os;
   unsigned char* dst = dyn_smem() + tab_off;

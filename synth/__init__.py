@@ -293,7 +293,7 @@ def batch_jobs(n_jobs: int = 64, seed: int = 1004, nvis_min: float = 1e4, nvis_m
                scale: float = 1.0) -> list[JobSpec]:
     """Channel / snapshot imaging jobs of uneven sizes: grid sizes from {512, 1024, 2048, 4096},
     visibility counts log-uniform in [nvis_min, nvis_max] (times `scale`), supports 7-31,
-    oversampling 4-8 and 8-64 w-planes. Snapshot jobs have many baselines and few samples,
+    oversampling 4, 6 or 8 and 8-64 w-planes. Snapshot jobs have many baselines and few samples,
     channel jobs one channel and long tracks; the cell size makes the longest baseline fill the
     grid to 95%."""
     rng = np.random.default_rng(seed)
@@ -303,7 +303,7 @@ def batch_jobs(n_jobs: int = 64, seed: int = 1004, nvis_min: float = 1e4, nvis_m
         nvis = float(np.exp(rng.uniform(np.log(nvis_min), np.log(nvis_max)))) * scale
         s_min = int(rng.integers(7, 32))
         s_max = int(rng.integers(s_min, 32))
-        os_ = int(rng.integers(4, 9))
+        os_ = int(rng.choice([4, 6, 8]))                    # even, as the kernel tables need
         n_w = int(rng.integers(8, 65))
         nchan = int(rng.choice([1, 2, 4]))
         n_ant = int(rng.integers(16, 129))
