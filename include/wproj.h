@@ -135,6 +135,34 @@ int wp_grid_noalloc(wp_ctx* ctx, const double* uvw, const double* freq, const vo
                     const float* weight, int64_t nrow, int32_t nchan, int32_t flags, void* grid,
                     double* sum_w, int64_t* n_dropped, void* stream);
 
+/* ---- the paper's baseline-ordered GPU gridding (a comparison variant) ---- */
+
+/* Rows grouped by baseline and time-ordered within each (Sec. 2.2): the baseline index of Eq. 5,
+ *   I_B = (-S^2 + 2 S N_ant + S)/2 + |I_ant1 - I_ant2|,  S = min(I_ant1, I_ant2)
+ * (autocorrelations counted, so I_B < N_ant (N_ant + 1)/2), the sample count C of every baseline
+ * and the start indices of Eq. 6 (exclusive prefix sums of C).
+ *   ant1, ant2 device [nrow] int32 antenna IDs in [0, n_ant); rows in time order (row index).
+ *   perm_out  device [nrow] int32: row indices, baseline after baseline, rising within one.
+ *   start_out device [N_ant (N_ant + 1)/2 + 1] uint32: Eq. 6, the row total at the end.
+ * Baselines of more than 4096 rows keep the order of an atomic scatter (still grouped).
+ * A row with an antenna ID outside [0, n_ant) belongs to no baseline: such rows fill
+ * perm_out after start_out[N_B] (in any order), so start_out[N_B] < nrow shows them.
+ * Errors: WP_EINVAL, WP_ENOMEM, WP_ECUDA. */
+int wp_baseline_order(wp_ctx* ctx, const int32_t* ant1, const int32_t* ant2, int64_t nrow, int32_t n_ant,
+                      int32_t* perm_out, uint32_t* start_out, void* stream);
+
+/* Gridding in the paper's GPU scheme (Sec. 2.2, Fig. 2): one thread block per (baseline, channel
+ * [, Hermitian partner]) and one thread per support tap; along the baseline's time samples a
+ * thread keeps its tap's sum in a register while the grid point stays the same and adds it to
+ * the grid atomically when the point moves. Same arguments and results as wp_grid (same float64
+ * coordinates), plus perm and start from wp_baseline_order; rows outside every baseline's
+ * range are not gridded (their weights still enter sum_w), entries of perm outside [0, nrow)
+ * are skipped. Supports up to 32. A comparison variant: wp_grid is the fast path. Errors as
+ * wp_grid, and WP_EINVAL for a support above 32. */
+int wp_grid_baseline(wp_ctx* ctx, const double* uvw, const double* freq, const void* vis, const float* weight,
+                     const int32_t* perm, const uint32_t* start, int32_t n_ant, int64_t nrow, int32_t nchan,
+                     int32_t flags, void* grid, double* sum_w, int64_t* n_dropped, void* stream);
+
 /* ---- many gridding jobs in one launch ---- */
 
 /* One gridding job: the arguments of one wp_grid call. Each job has its own context (its own

@@ -19,7 +19,8 @@ Pins (what ties this oracle to something other than itself) live in
 tests/test_oracle_*.py: the direct DFT dirty image including the (n-1) w-term, a unit
 point source, the w=0 separable reduction, the brute-force kernel DFT, Hermitian
 mirror symmetry, the sum-of-weights identity, the adjoint dot-product identity, the
-PSWF integral equation, and a brute-force image transform. No function here is
+PSWF integral equation, and a brute-force image transform; the baseline grouping of
+Sec. 2.2 (Eq. 5, Eq. 6) against the upper-triangle enumeration and brute-force sorting. No function here is
 "parity unpinned".
 """
 from .wproj import (  # noqa: F401
@@ -27,3 +28,4 @@ from .wproj import (  # noqa: F401
     screen, wkernel_unnormalised, wkernel_dft_bruteforce, wkernels, coords, grid, degrid,
     fft_to_image, image_to_grid_adjoint, dirty_image_dft, sum_weights,
 )
+from .baselines import baseline_index, baseline_order, baseline_starts, n_baselines  # noqa: F401

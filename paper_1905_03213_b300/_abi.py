@@ -18,7 +18,8 @@ _TABLES = {"f32": WP_TABLE_F32, "f16": WP_TABLE_F16, "bf16": WP_TABLE_BF16}
 SYMBOLS = ("wp_create", "wp_destroy", "wp_last_error", "wp_make_wkernels", "wp_grid", "wp_degrid",
            "wp_fft_to_image", "wp_plane_info", "wp_coords", "wp_wkernel_export", "wp_wkernel_norm",
            "wp_profile", "wp_profile_read", "wp_taper_eval_host", "wp_grid_noalloc", "wp_degrid_last", "wp_image_to_grid",
-           "wp_batch_create", "wp_batch_grid", "wp_batch_fused_jobs", "wp_batch_destroy")
+           "wp_batch_create", "wp_batch_grid", "wp_batch_fused_jobs", "wp_batch_destroy",
+           "wp_baseline_order", "wp_grid_baseline")
 PHASES = ("wkernels", "plan", "grid", "degrid", "fft", "image")
 
 
@@ -66,6 +67,8 @@ def _load():
     L.wp_batch_destroy.argtypes = [P]
     L.wp_batch_destroy.restype = None
     L.wp_plane_info.argtypes = [P, P, P]
+    L.wp_baseline_order.argtypes = [P, P, P, I64, I32, P, P, P]
+    L.wp_grid_baseline.argtypes = [P, P, P, P, P, P, P, I32, I64, I32, I32, P, P, P, P]
     L.wp_coords.argtypes = [P, P, P, I64, I32, I32, P, P]
     L.wp_wkernel_export.argtypes = [P, I32, I32, P, I64]
     L.wp_wkernel_norm.argtypes = [P, P]
@@ -226,6 +229,48 @@ class WProj:
         self._check(lib.wp_image_to_grid(self._h, _ptr(image), _ptr(sum_w), 1 if taper_correct else 0, _ptr(grid),
                                          self._stream(stream)), "wp_image_to_grid")
         return grid
+
+    def baseline_order(self, ant1, ant2, n_ant: int, stream=None):
+        """(perm [nrow] int32, start [N_ant (N_ant + 1)/2 + 1] uint32 as int32 storage): rows grouped
+        by the baseline index of Eq. 5, time-ordered within each baseline; start holds Eq. 6."""
+        import torch
+        _dev_tensor(ant1, torch.int32, "ant1")
+        nrow = ant1.shape[0]
+        _dev_tensor(ant2, torch.int32, "ant2", (nrow,))
+        nb = n_ant * (n_ant + 1) // 2
+        perm = torch.empty(nrow, dtype=torch.int32, device=ant1.device)
+        start = torch.empty(nb + 1, dtype=torch.int32, device=ant1.device)
+        self._check(lib.wp_baseline_order(self._h, _ptr(ant1), _ptr(ant2), nrow, n_ant, _ptr(perm), _ptr(start),
+                                          self._stream(stream)), "wp_baseline_order")
+        return perm, start
+
+    def grid_baseline(self, uvw, freq, vis, perm, start, n_ant: int, weight=None, grid=None, sum_w=None,
+                      n_dropped=None, hermitian_pairs: bool = False, accumulate: bool = False, stream=None):
+        """wp_grid's results through the paper's baseline-ordered kernel (perm, start from
+        baseline_order)."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        _dev_tensor(uvw, torch.float64, "uvw")
+        nrow = uvw.shape[0]
+        _dev_tensor(freq, torch.float64, "freq")
+        nchan = freq.shape[0]
+        _dev_tensor(vis, torch.complex64, "vis", (nrow, nchan))
+        _dev_tensor(perm, torch.int32, "perm", (nrow,))
+        _dev_tensor(start, torch.int32, "start", (n_ant * (n_ant + 1) // 2 + 1,))
+        if weight is not None:
+            _dev_tensor(weight, torch.float32, "weight", (nrow, nchan))
+        if grid is None:
+            grid = torch.empty((self.n, self.n), dtype=torch.complex64, device=dev)
+        _dev_tensor(grid, torch.complex64, "grid", (self.n, self.n))
+        if sum_w is None:
+            sum_w = torch.zeros(1, dtype=torch.float64, device=dev)
+        if n_dropped is None:
+            n_dropped = torch.zeros(1, dtype=torch.int64, device=dev)
+        flags = (WP_ACCUMULATE if accumulate else 0) | (WP_HERMITIAN_PAIRS if hermitian_pairs else 0)
+        self._check(lib.wp_grid_baseline(self._h, _ptr(uvw), _ptr(freq), _ptr(vis), _ptr(weight), _ptr(perm),
+                                         _ptr(start), n_ant, nrow, nchan, flags, _ptr(grid), _ptr(sum_w),
+                                         _ptr(n_dropped), self._stream(stream)), "wp_grid_baseline")
+        return grid, sum_w, n_dropped
 
     def coords(self, uvw, freq, hermitian_pairs: bool = False, stream=None):
         """[ngridded, 8] int32: U, V, plane, conj, keep, i0, j0, ox | oy << 16."""

@@ -113,6 +113,8 @@ struct wp_ctx {
   int32_t max_chan = 0;
   wp::DeviceBuffer records;
   wp::DeviceBuffer rounded;            // [3][nvis] int32 rounded coordinates (plan scratch)
+  wp::DeviceBuffer coord_scratch;      // wp_grid_baseline: [ngridded][8] int32 coordinates
+  wp::DeviceBuffer bl_scratch;         // wp_baseline_order: row baseline indices, counts, cursors
   wp::DeviceBuffer rec_index;          // [records] uint32: visibility index | partner << 31 (wp_grid)
   bool have_grid_plan = false;         // records/rec_index hold the last wp_grid's binning
   int64_t plan_nrow = 0;
@@ -166,6 +168,15 @@ cudaError_t launch_degrid(wp_ctx* ctx, const float2* grid, float2* vis_out, cons
 // register-holding degridding kernel (degrid2.cu); *used = false when the geometry is outside its limits
 cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* vis_out, const uint32_t* index,
                              cudaStream_t s, bool* used);
+// the paper's baseline-ordered gridding, a comparison variant (baseline.cu)
+cudaError_t launch_baseline_order(wp_ctx* ctx, const int32_t* ant1, const int32_t* ant2, int64_t nrow,
+                                  int32_t n_ant, int32_t* bidx, uint32_t* count, uint32_t* start,
+                                  uint32_t* cursor, int32_t* perm, cudaStream_t s);
+cudaError_t launch_grid_baseline(wp_ctx* ctx, const int32_t* coords, const uint32_t* start, const int32_t* perm,
+                                 int32_t n_ant, int32_t nchan, int64_t nrow, bool pairs, const float2* vis,
+                                 const float* weight, float2* grid, cudaStream_t s);
+cudaError_t launch_kept_sums(wp_ctx* ctx, const int32_t* coords, int64_t ng, int64_t nvis, const float* weight,
+                             cudaStream_t s);
 // imaging (image.cu)
 cudaError_t launch_taper_inverse(const double* taper_img, float* inv, int32_t n, cudaStream_t s);
 cudaError_t launch_image_pre(const float* image, const double* sum_w, const float* inv_taper, int32_t taper_correct,

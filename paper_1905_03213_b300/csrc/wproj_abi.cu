@@ -190,7 +190,8 @@ void wp_destroy(wp_ctx* ctx) {
                   ctx->d_stage,    ctx->d_quad,      ctx->d_tab64,     ctx->d_tab,      ctx->d_supp,
                   ctx->d_wplane,   ctx->d_tab_off,   ctx->d_tab64_off, ctx->d_quad_off, ctx->d_nu,
                   ctx->d_counts,   ctx->d_offsets,   ctx->d_cursor,    ctx->d_partials, ctx->d_chan,
-                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2, ctx->d_work, ctx->rounded.ptr, ctx->rec_index.ptr, ctx->d_suboff, ctx->d_lanetab, ctx->d_lanetab_off};
+                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2, ctx->d_work, ctx->rounded.ptr, ctx->rec_index.ptr, ctx->d_suboff, ctx->d_lanetab, ctx->d_lanetab_off,
+                  ctx->coord_scratch.ptr, ctx->bl_scratch.ptr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -503,6 +504,74 @@ int wp_coords(wp_ctx* ctx, const double* uvw, const double* freq, int64_t nrow, 
   WP_CUDA(ctx, wp::launch_channel_factors(freq, nchan, ctx->geo.os_l, ctx->geo.wscale, ctx->d_chan, s));
   ++ctx->launches;
   WP_CUDA(ctx, wp::launch_coords(ctx, uvw, nrow, nchan, pairs != 0, out, s));
+  return WP_OK;
+}
+
+int wp_baseline_order(wp_ctx* ctx, const int32_t* ant1, const int32_t* ant2, int64_t nrow, int32_t n_ant,
+                      int32_t* perm_out, uint32_t* start_out, void* stream) {
+  if (!ctx) return WP_EINVAL;
+  if (nrow < 0 || nrow > 0x7fffffff || n_ant < 1 || n_ant > 46000)
+    return fail(ctx, WP_EINVAL, "nrow must be in [0, 2^31) and n_ant in [1, 46000]");
+  if (!start_out || (nrow > 0 && (!ant1 || !ant2 || !perm_out)))
+    return fail(ctx, WP_EINVAL, "ant1, ant2, perm_out and start_out must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  WP_CUDA(ctx, cudaSetDevice(ctx->prm.device));
+  const int64_t nb = (int64_t)n_ant * (n_ant + 1) / 2;
+  int rc = ensure_buffer(ctx, ctx->bl_scratch, sizeof(int32_t) * (size_t)std::max<int64_t>(nrow, 1) +
+                                                   2 * sizeof(uint32_t) * (size_t)(nb + 1), "baseline scratch");
+  if (rc) return rc;
+  int32_t* bidx = (int32_t*)ctx->bl_scratch.ptr;
+  uint32_t* count = (uint32_t*)(bidx + std::max<int64_t>(nrow, 1));
+  uint32_t* cursor = count + nb + 1;
+  WP_CUDA(ctx, wp::launch_baseline_order(ctx, ant1, ant2, nrow, n_ant, bidx, count, start_out, cursor, perm_out, s));
+  return WP_OK;
+}
+
+int wp_grid_baseline(wp_ctx* ctx, const double* uvw, const double* freq, const void* vis, const float* weight,
+                     const int32_t* perm, const uint32_t* start, int32_t n_ant, int64_t nrow, int32_t nchan,
+                     int32_t flags, void* grid, double* sum_w, int64_t* n_dropped, void* stream) {
+  if (!ctx) return WP_EINVAL;
+  if (flags & ~(WP_ACCUMULATE | WP_HERMITIAN_PAIRS)) return fail(ctx, WP_EINVAL, "unknown flag bits");
+  if (!grid) return fail(ctx, WP_EINVAL, "grid must not be NULL");
+  if (nrow > 0 && (!vis || !perm || !start)) return fail(ctx, WP_EINVAL, "vis, perm and start must not be NULL");
+  if (n_ant < 1 || n_ant > 46000) return fail(ctx, WP_EINVAL, "n_ant must be in [1, 46000]");
+  if (*std::max_element(ctx->supp.begin(), ctx->supp.end()) > 32)
+    return fail(ctx, WP_EINVAL, "wp_grid_baseline takes supports up to 32");
+  const int pairs = (flags & WP_HERMITIAN_PAIRS) ? 1 : 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = check_vis_args(ctx, uvw, freq, nrow, nchan, pairs);
+  if (rc) return rc;
+  if (!ctx->have_kernels) return fail(ctx, WP_ESTATE, "wp_make_wkernels has not been called");
+  WP_CUDA(ctx, cudaSetDevice(ctx->prm.device));
+  if ((rc = ensure_channels(ctx, nchan))) return rc;
+  if (nrow > 0) {
+    WP_CUDA(ctx, wp::launch_channel_factors(freq, nchan, ctx->geo.os_l, ctx->geo.wscale, ctx->d_chan, s));
+    ++ctx->launches;
+  }
+  const int64_t nvis = nrow * nchan, ng = nvis * (pairs ? 2 : 1);
+  if ((rc = ensure_buffer(ctx, ctx->coord_scratch, sizeof(int32_t) * 8 * (size_t)std::max<int64_t>(ng, 1),
+                          "coordinate scratch")))
+    return rc;
+  const int32_t n = ctx->prm.n;
+  if (!(flags & WP_ACCUMULATE)) WP_CUDA(ctx, cudaMemsetAsync(grid, 0, sizeof(float2) * (size_t)n * n, s));
+  int32_t* coords = (int32_t*)ctx->coord_scratch.ptr;
+  {
+    Phase ph(ctx, WP_PHASE_PLAN, s);
+    if (nrow > 0) WP_CUDA(ctx, wp::launch_coords(ctx, uvw, nrow, nchan, pairs != 0, coords, s));
+    WP_CUDA(ctx, wp::launch_kept_sums(ctx, coords, ng, nvis, weight, s));
+  }
+  {
+    Phase ph(ctx, WP_PHASE_GRID, s);
+    if (nrow > 0)
+      WP_CUDA(ctx, wp::launch_grid_baseline(ctx, coords, start, perm, n_ant, nchan, nrow, pairs != 0,
+                                            (const float2*)vis, weight, (float2*)grid, s));
+  }
+  if (sum_w || n_dropped) {
+    k_store_scalars<<<1, 1, 0, s>>>(ctx->d_wsum, ctx->d_dropped, sum_w, (long long*)n_dropped,
+                                    (flags & WP_ACCUMULATE) ? 1 : 0);
+    WP_CUDA(ctx, cudaGetLastError());
+    ++ctx->launches;
+  }
   return WP_OK;
 }
 

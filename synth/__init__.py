@@ -129,6 +129,12 @@ def baseline_pairs(n_ant: int) -> tuple[np.ndarray, np.ndarray]:
     return a1.astype(np.int64), a2.astype(np.int64)
 
 
+def row_antennas(n_ant: int, n_time: int) -> tuple[np.ndarray, np.ndarray]:
+    """Antenna IDs (ant1, ant2) int32 of every row in uvw_metres' time-major row order."""
+    a1, a2 = baseline_pairs(n_ant)
+    return np.tile(a1, n_time).astype(np.int32), np.tile(a2, n_time).astype(np.int32)
+
+
 def hour_angles(n_time: int, duration_h: float) -> np.ndarray:
     """Sample centres H_k = -T/2 + (k + 1/2) T / n, centred on transit (rad)."""
     t = -duration_h / 2 + (np.arange(n_time) + 0.5) * duration_h / n_time
