@@ -26,14 +26,30 @@ def needs_build() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+    """Compiles every source to an object in parallel (one nvcc per file), then links the library."""
     if not force and not needs_build():
         return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = ["nvcc", "-shared", "-Xcompiler", "-fPIC", "-O3", "-std=c++17", "-lineinfo", *ARCH,
-           "-I", os.path.join(ROOT, "include"), "-o", tmp, *sources(), "-lcufft"] + (extra or [])
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.run(cmd, check=True)
+    from concurrent.futures import ThreadPoolExecutor
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    tag = os.getpid()
+    common = ["nvcc", "-Xcompiler", "-fPIC", "-O3", "-std=c++17", "-lineinfo", *ARCH, "-I", os.path.join(ROOT, "include")]
+
+    def compile_one(src: str) -> str:
+        obj = os.path.join(objdir, os.path.basename(src) + f".{tag}.o")
+        cmd = common + ["-c", src, "-o", obj] + (extra or [])
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        subprocess.run(cmd, check=True)
+        return obj
+
+    srcs = sources()
+    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(compile_one, srcs))
+    tmp = LIB + f".{tag}.tmp"
+    subprocess.run(["nvcc", "-shared", *ARCH, "-o", tmp, *objs, "-lcufft"], check=True)
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

@@ -201,7 +201,7 @@ __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
     const bool staged = s <= kMaxStagedS || tab_off + tbytes + sbytes + kStagedChunk * (int)sizeof(Record) <= a.smem_bytes;
     const int sub_off = tab_off + (staged ? tbytes : 0);
     const int rec_off = sub_off + sbytes;
-    const int cap = (a.smem_bytes - rec_off) / (int)sizeof(Record);
+    const int cap = min(kMaxChunk, (a.smem_bytes - rec_off) / (int)sizeof(Record));
     int ntiles = 1;
     const uint32_t seg_end = segment_end(a.offsets, a.nbins, bin, tx, a.g.ntx, pos, end, cap, a.group_tiles, &ntiles);
     const bool stage = staged && p != cur_plane;

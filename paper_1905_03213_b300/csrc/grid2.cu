@@ -193,7 +193,7 @@ __device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end) {
     const int tbytes = a.g.os * a.g.os * lay_class_bytes(s, TabElem<T>::E);
     const bool staged = s <= kMaxStagedS || tab_off + tbytes + kStagedChunk * (int)sizeof(Record) <= a.smem_bytes;
     const int rec_off = tab_off + (staged ? tbytes : 0);
-    const int cap = (a.smem_bytes - rec_off) / (int)sizeof(Record);
+    const int cap = min(kMaxChunk, (a.smem_bytes - rec_off) / (int)sizeof(Record));
     int ntiles = 1;
     const uint32_t seg_end = segment_end(a.offsets, a.nbins, bin, tx, a.g.ntx, pos, end, cap, a.group_tiles, &ntiles);
     const bool stage = staged && p != cur_plane;

@@ -22,6 +22,8 @@ constexpr int kStagedChunk = 2048;                            // records left ro
 constexpr int kMaxKeys = 4096;                                  // origins of one segment
 constexpr int kCountsBytes = ((kMaxKeys + 1) * 4 + 15) & ~15;  // shared-memory counters
 constexpr int kMinChunk = 512;
+constexpr int kSortPer = 16;                                  // records per thread in one sort
+constexpr int kMaxChunk = kThreads * kSortPer;                 // records of one sorted chunk, at most
 constexpr uint32_t kNoOrigin = 0xffffffffu;
 constexpr int kUnitsPerCta = 8;                              // work units per CTA, on average
 
@@ -117,7 +119,7 @@ __device__ __forceinline__ int64_t advance_bin(const uint32_t* __restrict__ offs
 }
 
 // In-place exclusive scan of the shared counters counts[0..n) by the whole block.
-__device__ void block_exclusive_scan(int n) {
+__device__ __forceinline__ void block_exclusive_scan(int n) {
   __shared__ uint32_t warp_sums[kWarps];
   uint32_t* counts = (uint32_t*)dyn_smem();
   const int per = (n + kThreads - 1) / kThreads;
@@ -327,41 +329,34 @@ __device__ __forceinline__ int sort_chunk(const uint4* __restrict__ grecs, const
   using L = Lay<S, T>;
   uint32_t* counts = (uint32_t*)dyn_smem();
   uint4* drec = (uint4*)(dyn_smem() + rec_off);
+  // the whole chunk is read in one round of independent loads (kSortPer per thread), so the
+  // sort waits for global memory once; the counters are cleared while the loads are in flight
+  uint4 rec[kSortPer];
+  uint32_t idx[kSortPer];
+#pragma unroll
+  for (int u = 0; u < kSortPer; ++u) {
+    const int r = threadIdx.x + u * kThreads;
+    const int rr = min(r, m - 1);                 // m >= 1: loads past the chunk repeat its last record
+    idx[u] = index ? index[c0 + rr] : 0u;
+    rec[u] = __ldcs(grecs + c0 + rr);
+  }
   for (int k = threadIdx.x; k <= keys; k += kThreads) counts[k] = 0u;
   __syncthreads();
-  // pass 1: histogram of the origin keys, 4 loads in flight
-  for (int r0 = threadIdx.x; r0 < m; r0 += 4 * kThreads) {
-    uint32_t z[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = r0 + u * kThreads;
-      z[u] = (r < m && !(index && (index[c0 + r] >> 31))) ? __ldcg(&grecs[c0 + r].z) : kNoOrigin;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (z[u] != kNoOrigin) atomicAdd(&counts[((int)(z[u] >> 16) - y0) * width + ((int)(z[u] & 0xffff) - x0)], 1u);
-  }
+  for (int u = 0; u < kSortPer; ++u)
+    if (threadIdx.x + u * kThreads < m && !(idx[u] >> 31))
+      atomicAdd(&counts[((int)(rec[u].z >> 16) - y0) * width + ((int)(rec[u].z & 0xffff) - x0)], 1u);
   __syncthreads();
   block_exclusive_scan(keys + 1);
   const int kept = (int)counts[keys];
-  // pass 2: decode each record into its sorted slot
-  for (int r0 = threadIdx.x; r0 < m; r0 += 4 * kThreads) {
-    uint4 rec[4];
-    uint32_t idx[4];
+  // decode each record into its sorted slot
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = r0 + u * kThreads;
-      idx[u] = (r < m && index) ? index[c0 + r] : 0u;
-      if (r < m) rec[u] = __ldcs(grecs + c0 + r);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (r0 + u * kThreads < m && !(idx[u] >> 31)) {
-        const int key = ((int)(rec[u].z >> 16) - y0) * width + ((int)(rec[u].z & 0xffff) - x0);
-        const int cls = (int)((rec[u].w >> 8) & 0xff) * os + (int)(rec[u].w & 0xff);
-        const uint32_t w = (uint32_t)(cls * L::CB) | (rec[u].w & 0x80000000u);
-        drec[atomicAdd(&counts[key], 1u)] = make_uint4(index ? idx[u] : rec[u].x, rec[u].y, rec[u].z, w);
-      }
+  for (int u = 0; u < kSortPer; ++u) {
+    if (threadIdx.x + u * kThreads < m && !(idx[u] >> 31)) {
+      const int key = ((int)(rec[u].z >> 16) - y0) * width + ((int)(rec[u].z & 0xffff) - x0);
+      const int cls = (int)((rec[u].w >> 8) & 0xff) * os + (int)(rec[u].w & 0xff);
+      const uint32_t w = (uint32_t)(cls * L::CB) | (rec[u].w & 0x80000000u);
+      drec[atomicAdd(&counts[key], 1u)] = make_uint4(index ? idx[u] : rec[u].x, rec[u].y, rec[u].z, w);
     }
   }
   __syncthreads();
