@@ -229,8 +229,8 @@ int wp_create(wp_ctx** out, const wp_params* p) {
   wp_ctx* ctx = new (std::nothrow) wp_ctx();
   if (!ctx) return fail(nullptr, WP_ENOMEM, "host allocation failed");
   ctx->prm = q;
-  if (ctx->prm.tile_x == 0) ctx->prm.tile_x = 16;
-  if (ctx->prm.tile_y == 0) ctx->prm.tile_y = 16;
+  if (ctx->prm.tile_x == 0) ctx->prm.tile_x = 32;
+  if (ctx->prm.tile_y == 0) ctx->prm.tile_y = 32;
   ctx->m = q.screen_m ? q.screen_m : std::max(65, 4 * q.support_max + 1);
   auto bail = [&](int code, const std::string& msg) {
     g_create_error = msg;
