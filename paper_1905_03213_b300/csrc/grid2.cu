@@ -221,7 +221,7 @@ __device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end) {
 
 template <class T>
 __global__ void __launch_bounds__(kThreads, 1) k_grid_v2(G2Args a) {
-  for_each_unit(a.offsets, a.costoff, a.nbins, a.nunits, a.work,
+  for_each_unit<true>(a.offsets, a.costoff, a.nbins, a.nunits, a.work,
                 [&](uint32_t beg, uint32_t end) { grid_range<T>(a, beg, end); });
 }
 

@@ -394,7 +394,11 @@ __device__ __forceinline__ uint32_t segment_end(const uint32_t* __restrict__ off
 // the records exactly. CTAs take units from work[0], the last one first; the last CTA to
 // finish leaves work[0] and work[1] zero for the next launch. body(beg, end) runs with the
 // whole CTA.
-template <class Body>
+//
+// kTapered: unit u covers [C (u / N)^2, C ((u + 1) / N)^2) instead, so the units taken first (the
+// highest u) are the largest, about twice the mean, and the last ones taken are small: the CTAs
+// finish within a small unit of each other.
+template <bool kTapered = false, class Body>
 __device__ __forceinline__ void for_each_unit(const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ costoff,
                                               int64_t nbins, int nunits, uint32_t* work, Body body) {
   __shared__ int unit;
@@ -413,8 +417,12 @@ __device__ __forceinline__ void for_each_unit(const uint32_t* __restrict__ offse
     const int u = unit;
     __syncthreads();
     if (u < 0) break;
-    const uint32_t beg = split((uint64_t)ctotal * u / nunits);
-    const uint32_t end = split((uint64_t)ctotal * (u + 1) / nunits);
+    // ctotal < 2^32 and nunits < 2^16 keep the products below 2^64
+    const uint64_t nn = kTapered ? (uint64_t)nunits * nunits : (uint64_t)nunits;
+    const uint64_t u0 = kTapered ? (uint64_t)u * u : (uint64_t)u;
+    const uint64_t u1 = kTapered ? (uint64_t)(u + 1) * (u + 1) : (uint64_t)(u + 1);
+    const uint32_t beg = split((uint64_t)ctotal * u0 / nn);
+    const uint32_t end = split((uint64_t)ctotal * u1 / nn);
     if (beg < end) body(beg, end);
   }
   if (threadIdx.x == 0) {
