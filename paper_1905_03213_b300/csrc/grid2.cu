@@ -61,17 +61,17 @@ struct Footprint {
     for (int k = 0; k < L::RPA; ++k) re[k] = im[k] = 0ull;
     tre = tim = 0.f;
   }
-  // Adds this lane's cells (column col0 + a, rows j0 + row0 + r) to the grid when `pred`.
-  __device__ __forceinline__ void flush(bool pred, float2* __restrict__ grid, int n, int j0, int col0, int a,
-                                        int row0) const {
-    if (!pred) return;
-    float2* p = grid + (int64_t)(j0 + row0) * n + col0 + a;
+  // Adds this lane's cells to the grid where `pred`: rows r < nrow of its column, the first at
+  // cell index idx (32-bit: n <= 32768), the next ones n cells apart. Predicated, no branch.
+  __device__ __forceinline__ void flush(bool pred, float2* __restrict__ grid, uint32_t idx, uint32_t n, int nrow) const {
 #pragma unroll
     for (int k = 0; k < L::RP; ++k) {
-      if (row0 + 2 * k < S) red_add2(p + (int64_t)(2 * k) * n, lo_of(re[k]), lo_of(im[k]));
-      if (row0 + 2 * k + 1 < S) red_add2(p + (int64_t)(2 * k + 1) * n, hi_of(re[k]), hi_of(im[k]));
+      red_add2_if(pred && 2 * k < nrow, grid + idx, lo_of(re[k]), lo_of(im[k]));
+      idx += n;
+      red_add2_if(pred && 2 * k + 1 < nrow, grid + idx, hi_of(re[k]), hi_of(im[k]));
+      idx += n;
     }
-    if (L::RT && row0 + 2 * L::RP < S) red_add2(p + (int64_t)(2 * L::RP) * n, tre, tim);
+    if (L::RT) red_add2_if(pred && 2 * L::RP < nrow, grid + idx, tre, tim);
   }
   // acc(a) <- acc(a + d); columns a + d >= S start at zero.
   __device__ __forceinline__ void slide(int d, int a) {
@@ -110,6 +110,10 @@ __device__ __forceinline__ void warp_grid(int tab_off, const unsigned char* gtab
   fp.zero();
   uint32_t cz = kNoOrigin;
   int col0 = 0, cj = 0;
+  // this lane's rows inside the footprint, and its offset from the origin's cell index
+  const int nrow = active ? min(L::R, S - row0) : 0;
+  const uint32_t lane_off = (uint32_t)row0 * (uint32_t)n + (uint32_t)a;
+  uint32_t cidx = 0;                               // cell index of this lane's first cell
 #pragma unroll(L::RP > 1 ? 2 : 4)
   for (int q = beg; q < end; ++q) {
     const uint4 rec = drec[q];
@@ -117,19 +121,16 @@ __device__ __forceinline__ void warp_grid(int tab_off, const unsigned char* gtab
     tv.load(tab + (rec.w & 0x7fffffffu), lane);
     if (rec.z != cz) {                             // warp-uniform: a new footprint origin
       const int i0 = rec.z & 0xffff, j0 = rec.z >> 16;
-      if (cz != kNoOrigin) {
-        const int d = i0 - col0;
-        if (j0 == cj && d > 0 && d < S) {
-          fp.flush(active && a < d, grid, n, cj, col0, a, row0);
-          fp.slide(d, a);
-        } else {
-          fp.flush(active, grid, n, cj, col0, a, row0);
-          fp.zero();
-        }
-      }
+      const int d = i0 - col0;
+      const bool slide = j0 == cj && (unsigned)(d - 1) < (unsigned)(S - 1);   // 0 < d < S on the same row
+      // a slide adds the d leaving columns to the grid, any other move every cell
+      fp.flush(cz != kNoOrigin && (!slide || a < d), grid, cidx, (uint32_t)n, nrow);
+      if (slide) fp.slide(d, a);
+      else fp.zero();
       cz = rec.z;
       col0 = i0;
       cj = j0;
+      cidx = (uint32_t)j0 * (uint32_t)n + (uint32_t)i0 + lane_off;
     }
     // acc.re += cr kr + be ki, acc.im += ci kr + de ki: c K, or c conj(K) for w < 0
     const uint32_t flip = (rec.w & 0x80000000u) ^ 0x80000000u;
@@ -152,8 +153,7 @@ __device__ __forceinline__ void warp_grid(int tab_off, const unsigned char* gtab
       fp.tim = fmaf(de, tv.ti, fp.tim);
     }
   }
-  if (cz == kNoOrigin) return;
-  fp.flush(active, grid, n, cj, col0, a, row0);
+  fp.flush(cz != kNoOrigin, grid, cidx, (uint32_t)n, nrow);
 }
 
 template <int S, class T>

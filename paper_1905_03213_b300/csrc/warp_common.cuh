@@ -172,6 +172,13 @@ __device__ __forceinline__ void red_add2(float2* p, float x, float y) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(x), "f"(y) : "memory");
 }
 
+// red_add2 where p is true: one predicated instruction, no branch.
+__device__ __forceinline__ void red_add2_if(bool pred, float2* p, float x, float y) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q red.global.add.v2.f32 [%0], {%1, %2};\n\t}"
+      ::"l"(p), "f"(x), "f"(y), "r"((uint32_t)pred) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long shfl_down2(unsigned long long v, int d) {
   const uint32_t lo = __shfl_down_sync(0xffffffffu, (uint32_t)v, d);
   const uint32_t hi = __shfl_down_sync(0xffffffffu, (uint32_t)(v >> 32), d);
