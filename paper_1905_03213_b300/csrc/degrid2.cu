@@ -229,7 +229,7 @@ __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
 
 template <class T>
 __global__ void __launch_bounds__(kThreads, 1) k_degrid_v2(D2Args a) {
-  for_each_unit(a.offsets, a.costoff, a.nbins, a.nunits, a.work,
+  for_each_unit<true>(a.offsets, a.costoff, a.nbins, a.nunits, a.work,
                 [&](uint32_t beg, uint32_t end) { degrid_range<T>(a, beg, end); });
 }
 
