@@ -45,6 +45,8 @@ extern "C" {
 /* wp_grid flags. */
 #define WP_ACCUMULATE      1  /* add into `grid` (and *sum_w, *n_dropped) instead of overwriting */
 #define WP_HERMITIAN_PAIRS 2  /* also grid each sample as W*conj(V) at -uvw */
+#define WP_KEEP_BINNING    4  /* wp_grid: keep this call's binning for wp_degrid_last (one more
+                                 4-byte store per gridded visibility: its visibility index) */
 
 typedef struct wp_ctx wp_ctx;
 
@@ -220,9 +222,10 @@ int wp_degrid(wp_ctx* ctx, const double* uvw, const double* freq, const void* gr
  * wp_grid added are skipped, dropped visibilities get 0.
  *   grid device [N][N] float2 (read only); vis_out device [nrow][nchan] float2 (overwritten),
  *   nrow and nchan those of the wp_grid call.
- * The binning stays valid until the context's next wp_grid, wp_grid_noalloc or wp_degrid.
- * Errors: WP_ESTATE when there is no such wp_grid call (none yet, or a later wp_degrid or
- * wp_grid_noalloc replaced its binning); WP_EINVAL, WP_ECUDA. */
+ * That wp_grid call must pass WP_KEEP_BINNING. The binning stays valid until the context's next
+ * wp_grid, wp_grid_noalloc or wp_degrid.
+ * Errors: WP_ESTATE when there is no such wp_grid call (none yet, one without WP_KEEP_BINNING,
+ * or a later wp_degrid or wp_grid_noalloc replaced its binning); WP_EINVAL, WP_ECUDA. */
 int wp_degrid_last(wp_ctx* ctx, const void* grid, void* vis_out, void* stream);
 
 /* Dirty image from the grid (the IFFT of Fig. 1 / Fig. 2) with the taper correction:

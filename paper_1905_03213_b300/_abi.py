@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(_HERE, "libwproj.so")
 
 WP_OK, WP_EINVAL, WP_ENOMEM, WP_ECUDA, WP_EOVERFLOW, WP_ESTATE = range(6)
 WP_TABLE_F32, WP_TABLE_F16, WP_TABLE_BF16 = 0, 1, 2
-WP_ACCUMULATE, WP_HERMITIAN_PAIRS = 1, 2
+WP_ACCUMULATE, WP_HERMITIAN_PAIRS, WP_KEEP_BINNING = 1, 2, 4
 _TABLES = {"f32": WP_TABLE_F32, "f16": WP_TABLE_F16, "bf16": WP_TABLE_BF16}
 
 # every function declared in include/wproj.h
@@ -153,8 +153,9 @@ class WProj:
         self._check(lib.wp_make_wkernels(self._h, self._stream(stream)), "wp_make_wkernels")
 
     def grid(self, uvw, freq, vis, weight=None, grid=None, sum_w=None, n_dropped=None,
-             hermitian_pairs: bool = False, accumulate: bool = False, stream=None):
-        """Returns (grid [N, N] complex64, sum_w [1] float64, n_dropped [1] int64), device tensors."""
+             hermitian_pairs: bool = False, accumulate: bool = False, keep_binning: bool = False, stream=None):
+        """Returns (grid [N, N] complex64, sum_w [1] float64, n_dropped [1] int64), device tensors.
+        keep_binning: keep the binning for degrid_last (WP_KEEP_BINNING)."""
         import torch
         dev = torch.device("cuda", self.device)
         _dev_tensor(uvw, torch.float64, "uvw")
@@ -171,11 +172,13 @@ class WProj:
             sum_w = torch.zeros(1, dtype=torch.float64, device=dev)
         if n_dropped is None:
             n_dropped = torch.zeros(1, dtype=torch.int64, device=dev)
-        flags = (WP_ACCUMULATE if accumulate else 0) | (WP_HERMITIAN_PAIRS if hermitian_pairs else 0)
+        flags = ((WP_ACCUMULATE if accumulate else 0) | (WP_HERMITIAN_PAIRS if hermitian_pairs else 0)
+                 | (WP_KEEP_BINNING if keep_binning else 0))
         self._last_grid_shape = None
         self._check(lib.wp_grid(self._h, _ptr(uvw), _ptr(freq), _ptr(vis), _ptr(weight), nrow, nchan, flags,
                                 _ptr(grid), _ptr(sum_w), _ptr(n_dropped), self._stream(stream)), "wp_grid")
-        self._last_grid_shape = (nrow, nchan)
+        if keep_binning:
+            self._last_grid_shape = (nrow, nchan)
         return grid, sum_w, n_dropped
 
     def degrid(self, uvw, freq, grid, vis_out=None, stream=None):
@@ -193,7 +196,8 @@ class WProj:
         return vis_out
 
     def degrid_last(self, grid, vis_out=None, stream=None):
-        """Degrids the visibilities of the most recent grid() call, reusing its binning (wp_degrid_last)."""
+        """Degrids the visibilities of the most recent grid(..., keep_binning=True) call, reusing its
+        binning (wp_degrid_last)."""
         import torch
         _dev_tensor(grid, torch.complex64, "grid", (self.n, self.n))
         shape = getattr(self, "_last_grid_shape", None)

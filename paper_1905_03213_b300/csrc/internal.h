@@ -142,7 +142,7 @@ cudaError_t launch_taper_eval(const double* d_leg, int ncoef, double* out, int64
 cudaError_t launch_channel_factors(const double* freq, int32_t nchan, double os_l, double wscale,
                                    double* d_chan, cudaStream_t s);
 cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const float* weight,
-                        int64_t nrow, int32_t nchan, bool pairs, bool for_degrid, cudaStream_t s);
+                        int64_t nrow, int32_t nchan, bool pairs, bool for_degrid, bool keep_index, cudaStream_t s);
 // per-bin work estimate (fixed cost per non-empty bin + records x (S_p^2 + per-record cost)), scanned
 cudaError_t launch_bin_costs(wp_ctx* ctx, cudaStream_t s);
 cudaError_t launch_coords(wp_ctx* ctx, const double* uvw, int64_t nrow, int32_t nchan, bool pairs,

@@ -102,7 +102,7 @@ extern "C" int wp_grid_noalloc(wp_ctx* ctx, const double* uvw, const double* fre
   if (e == cudaSuccess && nrow > 0)
     e = wp::launch_channel_factors(freq, nchan, ctx->geo.os_l, ctx->geo.wscale, ctx->d_chan, s);
   if (e == cudaSuccess)
-    e = wp::launch_plan(ctx, uvw, (const float2*)vis, weight, nrow, nchan, pairs != 0, false, s);
+    e = wp::launch_plan(ctx, uvw, (const float2*)vis, weight, nrow, nchan, pairs != 0, false, false, s);
   if (e == cudaSuccess) e = wp::launch_grid(ctx, (float2*)grid, s);
   if (e == cudaSuccess && (sum_w || n_dropped)) {
     k_noalloc_scalars<<<1, 1, 0, s>>>(ctx->d_wsum, ctx->d_dropped, sum_w, (long long*)n_dropped,

@@ -386,7 +386,8 @@ cudaError_t launch_channel_factors(const double* freq, int32_t nchan, double os_
 }
 
 cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const float* weight, int64_t nrow,
-                        int32_t nchan, bool pairs, bool for_degrid, cudaStream_t s) {
+                        int32_t nchan, bool pairs, bool for_degrid, bool keep_index,
+                        cudaStream_t s) {
   const int64_t nvis = nrow * nchan;
   cudaError_t e;
   const int64_t nsub = ctx->nbins << ctx->nsub_log2;
@@ -396,9 +397,10 @@ cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const
   const int blocks = grid_blocks(nvis, ctx->nsm);
   // pass 1 keeps the rounded coordinates for pass 3 when the context's scratch holds them
   int32_t* rounded = ctx->rounded.bytes >= (size_t)nvis * 12 ? (int32_t*)ctx->rounded.ptr : nullptr;
-  // a gridding plan also records each record's visibility index, for wp_degrid_last
+  // a gridding plan asked to keep its binning also records each record's visibility index, for
+  // wp_degrid_last
   const size_t nrec = (size_t)nvis * (pairs ? 2 : 1);
-  uint32_t* index = (!for_degrid && ctx->rec_index.bytes >= nrec * 4) ? (uint32_t*)ctx->rec_index.ptr : nullptr;
+  uint32_t* index = (keep_index && !for_degrid && ctx->rec_index.bytes >= nrec * 4) ? (uint32_t*)ctx->rec_index.ptr : nullptr;
   ctx->launches += 4 + (nvis > 0 ? 2 : 0);  // prefix sum (3), bin offsets, histogram and scatter
   if (nvis > 0) {
     k_histogram<<<blocks, 256, 0, s>>>(uvw, ctx->d_chan, for_degrid ? nullptr : weight, nvis, nchan, pairs ? 1 : 0,

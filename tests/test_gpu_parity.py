@@ -260,7 +260,7 @@ def test_degrid_parity(torch_cuda, which, table):
 
 @pytest.mark.parametrize("pairs,table", [(False, "f32"), (True, "f32"), (True, "f16")])
 def test_degrid_last_reuses_grid_binning(torch_cuda, pairs, table):
-    """wp_degrid_last after wp_grid equals wp_degrid on the same visibilities, element for
+    """wp_degrid_last after wp_grid(WP_KEEP_BINNING) equals wp_degrid on the same visibilities, element for
     element (the partners wp_grid added are skipped, dropped visibilities are 0), and against
     the oracle within the degridding tolerance."""
     import torch
@@ -269,7 +269,12 @@ def test_degrid_last_reuses_grid_binning(torch_cuda, pairs, table):
     wp = make_wproj(case, table=table)
     uvw, f, vis, wt = to_dev(case)
     G = torch.from_numpy(synth.random_grid(case.prm.n, 21)).cuda()
+    # without WP_KEEP_BINNING the binning is not kept: degrid_last is refused
     wp.grid(uvw, f, vis, wt, hermitian_pairs=pairs)
+    with pytest.raises(W.WProjError):
+        wp.degrid_last(G)
+    assert W.lib.wp_degrid_last(wp._h, G.data_ptr(), G.data_ptr(), None) == W.WP_ESTATE
+    wp.grid(uvw, f, vis, wt, hermitian_pairs=pairs, keep_binning=True)
     last = wp.degrid_last(G)
     own = wp.degrid(uvw, f, G)
     assert torch.equal(last, own)
@@ -316,7 +321,7 @@ def test_profile_counts_phases_and_launches(torch_cuda):
     # + (1 channel + 6 plan + 4 work-estimate scan + 1 degrid) + 1 image
     assert launches == 32
     # degridding the gridded visibilities again reuses wp_grid's binning: no plan phase
-    g, sw, _ = wp.grid(uvw, f, vis, wt)
+    g, sw, _ = wp.grid(uvw, f, vis, wt, keep_binning=True)
     wp.profile_read()
     wp.degrid_last(g)
     ms, cnt, launches = wp.profile_read()
