@@ -25,7 +25,7 @@ constexpr int kMinChunk = 512;
 constexpr int kSortPer = 16;                                  // records per thread in one sort
 constexpr int kMaxChunk = kThreads * kSortPer;                 // records of one sorted chunk, at most
 constexpr uint32_t kNoOrigin = 0xffffffffu;
-constexpr int kUnitsPerCta = 8;                              // work units per CTA, on average
+constexpr int kUnitsPerCta = 6;                              // work units per CTA, on average
 
 
 // Lane layout for support S <= 16: G row groups of S lanes; lane g*S + a holds rows g*R ..
