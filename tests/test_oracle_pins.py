@@ -342,3 +342,55 @@ def test_wterm_matters():
     inner = (slice(q, 3 * q), slice(q, 3 * q))
     err2d = np.abs(img[inner] - ref2d[inner]).max() / np.abs(ref2d).max()
     assert err2d > 20 * _wproj_vs_dft(9)
+
+
+# ---------------------------------------------------------------- pins added for the remaining parts
+@pytest.mark.parametrize("n_w,s_min,s_max,expect", [
+    (1, 9, 9, [9]),                       # one plane: the paper's single full support (Sec. 3.1)
+    (23, 9, 9, [9] * 23),                 # S_min == S_max: every plane the same
+    (5, 8, 16, [8, 10, 12, 14, 16]),      # 8 p / 4 exact integers
+    (5, 7, 9, [7, 7, 8, 9, 9]),           # 2 p / 4 = 0, .5, 1, 1.5, 2: ties go to the even integer
+    (3, 8, 9, [8, 8, 9]),                 # 1 p / 2 = 0, .5, 1: the tie at p = 1 rounds down to 0
+    (32, 8, 16, None),                    # checked entry by entry below
+])
+def test_plane_supports_hand_worked(n_w, s_min, s_max, expect):
+    """S_p = S_min + rint((S_max - S_min) p / (Nw - 1)) with round-half-to-even, against
+    values worked out by hand (a half-up or floor rule fails the tie rows)."""
+    got = wproj.plane_supports(n_w, s_min, s_max).tolist()
+    if expect is not None:
+        assert got == expect
+        return
+    # 8 p / 31: p = 1 -> 0.258 (8), p = 2 -> 0.516 (9), p = 4 -> 1.032 (9), p = 6 -> 1.548 (10),
+    # p = 29 -> 7.484 (15), p = 30 -> 7.742 (16), p = 31 -> 8 (16)
+    assert len(got) == 32
+    for p, s in {0: 8, 1: 8, 2: 9, 4: 9, 6: 10, 29: 15, 30: 16, 31: 16}.items():
+        assert got[p] == s, (p, got[p], s)
+
+
+def test_hermitian_pairs_grid_is_hermitian(parity_case):
+    """A grid made with hermitian_pairs=True holds every sample and its conjugate at -uvw, so
+    G[(N - h) % N, (N - g) % N] = conj G[h, g] wherever no footprint sits at a rounding tie or
+    touches row/column 0 (whose mirror would be N). This pins `gridded_values` (the partner's
+    W conj(V)) and the partner coordinates of `coords` together: dropping the conjugate, or
+    giving the partner the original's conj flag or position, breaks the symmetry."""
+    cfg, ob, prm, tabs = parity_case
+    vis, wt = synth.random_visibilities(ob.uvw.shape[0], 1, 13)
+    crd = oracle.coords(ob.uvw, ob.freqs, prm, hermitian_pairs=True)
+    n_s = crd["nvis"]
+    half = crd["support"] * prm.os // 2
+    x = crd["U"] + prm.n // 2 * prm.os
+    y = crd["V"] + prm.n // 2 * prm.os
+    tie = ((x - half) % prm.os == 0) | ((y - half) % prm.os == 0)
+    ok = crd["keep"] & ~tie & (crd["i0"] > 0) & (crd["j0"] > 0)
+    both = ok[:n_s] & ok[n_s:]                 # a sample and its partner both qualify
+    assert both.sum() > 1000
+    crd["keep"] = np.concatenate([both, both])
+    c = wproj.gridded_values(vis, wt, crd)
+    g = oracle.grid(crd, c, tabs, prm)
+    n = prm.n
+    idx = (n - np.arange(n)) % n
+    np.testing.assert_allclose(g[np.ix_(idx, idx)], np.conj(g), rtol=0, atol=1e-12 * np.abs(g).max())
+    # the same grid without the partners is far from Hermitian (the check has teeth)
+    crd["keep"] = np.concatenate([both, np.zeros_like(both)])
+    g1 = oracle.grid(crd, c, tabs, prm)
+    assert np.abs(g1[np.ix_(idx, idx)] - np.conj(g1)).max() > 0.1 * np.abs(g1).max()
