@@ -37,8 +37,17 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
 METRIC = "gridded visibilities/s (whole W-projection step: kernels, coordinates+sort, grid, degrid, FFT+taper)"
-WORKLOAD = ("fp32: 128 ants / 5 km, 4 ch 1.0-1.4 GHz, 480 samples / 8 h -> 15.6M samples + Hermitian "
-            "conjugates = 31.2M gridded vis; 2048^2 @ 1\", 32 w-planes, support 8-16, os 8")
+WORKLOADS = {
+    "fp32": ("fp32: 128 ants / 5 km, 4 ch 1.0-1.4 GHz, 480 samples / 8 h -> 15.6M samples + Hermitian "
+             "conjugates = 31.2M gridded vis; 2048^2 @ 1\", 32 w-planes, support 8-16, os 8"),
+    "mixed": ("mixed: 256 ants / 10 km, 16 ch 1.0-1.4 GHz, 720 samples / 8 h -> 376M vis; 4096^2 @ 0.5\", "
+              "64 w-planes, support 8-32, os 8"),
+    "diff": "diff: 64 ants / 5 km, 1 ch 1.4 GHz, 496 samples / 8 h -> 1.0M vis; 2048^2 @ 1\", 32 w-planes, support 12, os 8",
+}
+
+
+def workload_name(config: str) -> str:
+    return WORKLOADS.get(config, config)
 
 
 def measured_peaks():
@@ -132,24 +141,55 @@ def run_gpu(args):
     uvw, vis, wt = ob.uvw.contiguous(), ob.vis.contiguous(), ob.weight.contiguous()
     freq = torch.as_tensor(ob.freqs, dtype=torch.float64, device=dev)
     tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (0, 0)
-    wp = W.WProj(n=cfg.n, cell=cfg.cell, n_w=cfg.n_w, w_max=ob.w_max, support_min=cfg.s_min,
-                 support_max=cfg.s_max, oversample=cfg.oversample, table=args.table, tile=tile, device=local)
     n = cfg.n
     grid = torch.empty((n, n), dtype=torch.complex64, device=dev)
     image = torch.empty((n, n), dtype=torch.float32, device=dev)
     pred = torch.empty_like(vis)
     sum_w = torch.zeros(1, dtype=torch.float64, device=dev)
     ndrop = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
 
-    def step():
-        wp.make_wkernels()
-        wp.grid(uvw, freq, vis, wt, grid=grid, sum_w=sum_w, n_dropped=ndrop, hermitian_pairs=cfg.hermitian_pairs)
-        wp.degrid(uvw, freq, grid, vis_out=pred)
-        wp.fft_to_image(grid, sum_w, image=image)
+    def make(table):
+        return W.WProj(n=cfg.n, cell=cfg.cell, n_w=cfg.n_w, w_max=ob.w_max, support_min=cfg.s_min,
+                       support_max=cfg.s_max, oversample=cfg.oversample, table=table, tile=tile, device=local)
 
-    # untimed: the work counts (kept visibilities and taps) from the library's own coordinates
-    step()
+    def stepper(wp):
+        def step():
+            wp.make_wkernels()
+            wp.grid(uvw, freq, vis, wt, grid=grid, sum_w=sum_w, n_dropped=ndrop,
+                    hermitian_pairs=cfg.hermitian_pairs, keep_binning=True)
+            wp.degrid_last(grid, vis_out=pred)
+            wp.fft_to_image(grid, sum_w, image=image)
+        return step
+
+    def timed_steps(wp, steps, warmup, clocks=None):
+        step = stepper(wp)
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        wp.profile(True)
+        wp.profile_read()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with (clocks if clocks is not None else _NoClock()):
+            e0.record(stream)
+            for _ in range(steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = e0.elapsed_time(e1) / steps
+        phase_ms, phase_cnt, launches = wp.profile_read()
+        wp.profile(False)
+        return ms, {k: phase_ms[k] / max(1, phase_cnt[k]) for k in phase_ms}, launches
+
+    wp = make(args.table)
+    stepper(wp)()                                   # untimed first step
     torch.cuda.synchronize()
+    # the work counts (kept visibilities and taps) from the library's own coordinates
     sup, _ = wp.plane_info()
     sup_t = torch.as_tensor(sup, device=dev).long()
     crd = wp.coords(uvw, freq, hermitian_pairs=cfg.hermitian_pairs)
@@ -162,27 +202,8 @@ def run_gpu(args):
     taps_degrid = int((sup_t[crd[:, 2][keep].long()] ** 2).sum().item())
     del crd, keep
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    wp.profile(True)
-    wp.profile_read()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    ms_step = e0.elapsed_time(e1) / args.steps
-    phase_ms, phase_cnt, launches = wp.profile_read()
-    wp.profile(False)
+    clk = ClockSampler(local)
+    ms_step, phases, launches = timed_steps(wp, args.steps, args.warmup, clocks=clk)
     if world > 1:
         t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -195,8 +216,7 @@ def run_gpu(args):
             torch.distributed.destroy_process_group()
         return None
 
-    grid_ms = phase_ms["grid"] / max(1, phase_cnt["grid"])
-    degrid_ms = phase_ms["degrid"] / max(1, phase_cnt["degrid"])
+    grid_ms, degrid_ms = phases["grid"], phases["degrid"]
     peaks = measured_peaks()
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_fp32 = fp32_peak_tflops(nsm)
@@ -205,6 +225,13 @@ def run_gpu(args):
     # 8-byte cells read and written once, the plane tables read once
     tab_bytes = sum((int(s) * cfg.oversample) ** 2 * (8 if args.table == "f32" else 4) for s in sup)
     alg_bytes = kept * 16 + 2 * 8 * n * n + tab_bytes
+    probe = {}
+    if not args.no_probe:
+        tf2, ms2 = W.probe_fp32_fma(local, packed=True, iters=100_000, reps=5)
+        tf1, _ = W.probe_fp32_fma(local, packed=False, iters=100_000, reps=5)
+        probe = {"packed_fma2_tflops": tf2, "scalar_fma_tflops": tf1, "frac_of_measured_fma2": achieved / tf2,
+                 "note": "project-written FMA probe (wp_probe_fp32_fma), 16 independent chains per thread, "
+                         f"{ms2:.1f} ms per launch"}
     out = {
         "metric": METRIC,
         "value": kept * world / (ms_step * 1e-3),
@@ -218,35 +245,93 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32" if args.table == "f32" else f"f32 ({args.table} tables)",
         "data": "synthetic (seeded array/uvw/sky generators; values from 200 point sources + noise)",
-        "config": {"workload": WORKLOAD if not args.rows else f"{WORKLOAD}; first {args.rows} rows only",
+        "config": {"workload": workload_name(args.config) + (f"; first {args.rows} rows only" if args.rows else ""),
                    "table": args.table, "tile": args.tile or "default", "gridded_visibilities": kept,
-                   "degridded_visibilities": kept_degrid, "l2": "inputs (0.4 GB) larger than L2; no flush",
+                   "degridded_visibilities": kept_degrid,
+                   "l2": "inputs larger than L2 (0.4 GB fp32, 4.5 GB mixed); no flush",
+                   "degrid": "wp_degrid_last: degrids the gridded samples with the gridding call's binning",
                    "parallelism": f"{world} independent job(s)"},
         "taps_per_s": (taps_grid + taps_degrid) * world / (ms_step * 1e-3),
-        "phases_ms": {k: phase_ms[k] / max(1, phase_cnt[k]) for k in phase_ms},
+        "phases_ms": phases,
         "grid_kernel": {"ms": grid_ms, "vis_per_s": kept / (grid_ms * 1e-3), "taps_per_s": taps_grid / (grid_ms * 1e-3),
                         "taps": taps_grid},
         "degrid_kernel": {"ms": degrid_ms, "vis_per_s": kept_degrid / (degrid_ms * 1e-3),
-                          "taps_per_s": taps_degrid / (degrid_ms * 1e-3), "taps": taps_degrid},
+                          "taps_per_s": taps_degrid / (degrid_ms * 1e-3), "taps": taps_degrid,
+                          "frac_of_fp32_peak": 8.0 * taps_degrid / (degrid_ms * 1e-3) / 1e12 / peak_fp32},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                     "frac": achieved / peak_fp32, "traffic": profiled_traffic(args.table, args.rows),
+                     "frac": achieved / peak_fp32, "traffic": profiled_traffic(args.table, args.rows, args.config),
                      "traffic_note": f"DRAM bytes per launch from the ncu summary in {GRID_PROFILE}",
-                     "kernel": f"k_grid_v2<{args.table}> (warp-synchronous register-accumulating gridding scatter, 8 flop per tap)",
-                     "peak_note": "FP32 FMA peak derived from unit counts (148 SMs x 128 lanes x 2 x 2.032 GHz)",
+                     "kernel": f"grid kernel <{args.table}> (warp-synchronous register-accumulating gridding scatter, 8 flop per tap)",
+                     "peak_note": f"FP32 FMA peak derived from unit counts ({nsm} SMs x 128 lanes x 2 x 2.032 GHz)",
+                     "peak_measured": probe,
                      "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / (grid_ms * 1e-3) / 1e9,
                              "peak_gbs": peaks.get("hbm_gbs"), "peak_note": "of measured"}},
         "clocks": clk.summary(),
         "gpu_launches": int(launches),
         "e2e": e2e,
     }
-    if not args.no_cpu_baseline and world == 1:
-        cb = cpu_baseline(args)
-        cb.pop("seconds", None)
-        cb.pop("kept", None)
+    if world == 1 and not args.no_cpu_baseline:
+        rows = cpu_sample_rows(cfg, args.cpu_vis)
+        sp = cpu_sample_from_device(cfg, rows, uvw, freq, vis, wt, ob.w_max)
+        cb, res = cpu_baseline(args, sp, keep=True)
+        cb["single_thread"] = single_thread_grid_rate(sp, res)
         out["cpu_baseline"] = cb
+        out["error"] = {args.table: error_figures(wp, sp, res)}
+        if args.variants:
+            out["mixed_vs_fp32"] = table_variants(args, make, timed_steps, sp, res, kept, taps_grid, grid_ms,
+                                                  ms_step, out["error"])
     if world > 1:
         torch.distributed.destroy_process_group()
     return out
+
+
+class _NoClock:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        pass
+
+
+def table_variants(args, make, timed_steps, sp, res, kept, taps, grid_ms, ms_step, errors):
+    """The same step with each kernel-table precision, on the same workload: throughput and
+    the error against the float64 oracle on the sample, side by side."""
+    rows = {args.table: {"ms_per_step": ms_step, "grid_kernel_ms": grid_ms, "vis_per_s": kept / (ms_step * 1e-3),
+                         "grid_taps_per_s": taps / (grid_ms * 1e-3), "error": errors[args.table]}}
+    for table in ("f32", "f16", "bf16"):
+        if table in rows:
+            continue
+        wp = make(table)
+        ms, ph, _ = timed_steps(wp, args.steps, args.warmup)
+        rows[table] = {"ms_per_step": ms, "grid_kernel_ms": ph["grid"], "vis_per_s": kept / (ms * 1e-3),
+                       "grid_taps_per_s": taps / (ph["grid"] * 1e-3), "error": error_figures(wp, sp, res)}
+        wp.close()
+    base = rows["f32"]
+    for table, r in rows.items():
+        r["step_speedup_vs_f32"] = base["ms_per_step"] / r["ms_per_step"]
+        r["grid_speedup_vs_f32"] = base["grid_kernel_ms"] / r["grid_kernel_ms"]
+        r["meets_tolerance"] = r["error"]["image_corrected_inner"]["max"] <= (1e-5 if table == "f32" else 1e-3)
+    return rows
+
+
+def run_fp32peak(args):
+    """The FP32 FMA roofline denominator, measured by the project's probe kernel."""
+    import torch
+    import paper_1905_03213_b300 as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    W.probe_fp32_fma(0, packed=True, iters=20_000, reps=2)
+    with ClockSampler(0) as clk:
+        tf2, ms2 = W.probe_fp32_fma(0, packed=True, iters=400_000, reps=args.steps)
+        tf1, ms1 = W.probe_fp32_fma(0, packed=False, iters=400_000, reps=args.steps)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    return {"metric": "FP32 FMA throughput (roofline denominator of the gridding scatter)", "value": tf2,
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": ms2,
+            "higher_is_better": True, "dtype": "f32", "data": "none (register-only FMA chains)",
+            "config": {"workload": "fp32peak: every SM at full occupancy, 16 independent FMA chains per thread"},
+            "packed_fma2_tflops": tf2, "scalar_fma_tflops": tf1, "scalar_ms_per_launch": ms1,
+            "unit_count_peak_tflops": fp32_peak_tflops(nsm), "frac_of_unit_count_peak": tf2 / fp32_peak_tflops(nsm),
+            "clocks": clk.summary()}
 
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -254,10 +339,10 @@ GRID_KERNEL_SOURCES = ("paper_1905_03213_b300/csrc/grid2.cu", "paper_1905_03213_
 GRID_PROFILE = "profiles/k_grid_v2_fp32_workload.md"
 
 
-def profiled_traffic(table: str, rows: int):
+def profiled_traffic(table: str, rows: int, config: str = "fp32"):
     """DRAM bytes of one gridding launch on the full fp32 workload, as the committed ncu summary
     states them, or None when the summary was taken on other kernel sources (or another case)."""
-    if rows or table != "f32":
+    if rows or table != "f32" or config != "fp32":
         return None
     h = hashlib.sha256()
     try:
@@ -293,8 +378,8 @@ def run_e2e(wp, uvw, vis, wt, freq, grid, sum_w, ndrop, pred, image, cfg, args, 
         d_wt.copy_(h_wt, non_blocking=True)
         wp.make_wkernels()
         wp.grid(d_uvw, d_freq, d_vis, d_wt, grid=grid, sum_w=sum_w, n_dropped=ndrop,
-                hermitian_pairs=cfg.hermitian_pairs)
-        wp.degrid(d_uvw, d_freq, grid, vis_out=pred)
+                hermitian_pairs=cfg.hermitian_pairs, keep_binning=True)
+        wp.degrid_last(grid, vis_out=pred)
         wp.fft_to_image(grid, sum_w, image=image)
         h_img.copy_(image, non_blocking=True)
 
@@ -317,37 +402,129 @@ def cpu_sample_rows(cfg, target_vis):
     return max(1, min(cfg.n_rows, target_vis // len(cfg.freqs)))
 
 
-def cpu_baseline(args, rows=None):
-    """The float64 oracle on the host cores over a bounded sample of the workload (its first
-    `rows` rows = the first time samples of every baseline), the same step as on the GPU:
-    kernels, coordinates, gridding, degridding, image."""
+class CpuSample:
+    """The oracle's bounded sample of the workload: its first `rows` rows (the first time
+    samples of every baseline) as host arrays, with the planes of the full observation."""
+
+    def __init__(self, cfg, rows, uvw, freqs, vis, weight, w_max):
+        import oracle
+        self.cfg, self.rows = cfg, rows
+        self.uvw, self.freqs, self.vis, self.weight, self.w_max = uvw, freqs, vis, weight, w_max
+        self.prm = oracle.Params(cfg.n, cfg.cell, cfg.n_w, w_max, cfg.s_min, cfg.s_max, cfg.oversample)
+
+
+def cpu_sample_from_host(cfg, rows):
+    """Sample made on the host by the numpy generators (the reference arm, no GPU)."""
     import synth
-    import oracle
-    from oracle import wproj
-    cfg = synth.config(args.config)
-    rows = rows or cpu_sample_rows(cfg, args.cpu_vis)
     ob = synth.observe(cfg, rows=rows)
     # w_max of the full observation, so the planes match the GPU run
     enu = synth.antenna_enu(cfg.n_ant, cfg.radius_m, cfg.height_m, np.random.default_rng(cfg.seed))
     uvw_all = synth.uvw_metres(enu, synth.SITE_LAT, cfg.dec, synth.hour_angles(cfg.n_time, cfg.duration_h))
     w_max = float(np.max(np.abs(uvw_all[:, 2])) * np.max(cfg.freqs) / synth.C_LIGHT)
-    prm = oracle.Params(cfg.n, cfg.cell, cfg.n_w, w_max, cfg.s_min, cfg.s_max, cfg.oversample)
+    return CpuSample(cfg, rows, ob.uvw, np.asarray(ob.freqs), ob.vis, ob.weight, w_max)
+
+
+def cpu_sample_from_device(cfg, rows, uvw, freq, vis, wt, w_max):
+    """Sample copied from the GPU run's own inputs (the same stored values on both sides)."""
+    return CpuSample(cfg, rows, uvw[:rows].cpu().numpy(), freq.cpu().numpy(), vis[:rows].cpu().numpy(),
+                     wt[:rows].cpu().numpy(), w_max)
+
+
+def host_threads():
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    threads = max(1, min(cores, 32))    # each OpenMP private float64 grid is 67 MB at 2048^2
-    t0 = time.perf_counter()
+    return cores, max(1, min(cores, 32))    # each OpenMP private float64 grid is 67 MB at 2048^2
+
+
+def oracle_step(sp: CpuSample, threads: int, keep=False):
+    """One pass of the whole path by the float64 oracle (kernels, coordinates, gridding,
+    degridding of the grid, image), with the time of each part."""
+    import oracle
+    from oracle import wproj
+    cfg, prm = sp.cfg, sp.prm
+    t = [time.perf_counter()]
     tabs, _ = oracle.wkernels(prm)
-    crd = oracle.coords(ob.uvw, ob.freqs, prm, hermitian_pairs=cfg.hermitian_pairs)
-    c = wproj.gridded_values(ob.vis, ob.weight, crd)
+    t.append(time.perf_counter())
+    crd = oracle.coords(sp.uvw, sp.freqs, prm, hermitian_pairs=cfg.hermitian_pairs)
+    crd1 = oracle.coords(sp.uvw, sp.freqs, prm)
+    c = wproj.gridded_values(sp.vis, sp.weight, crd)
+    t.append(time.perf_counter())
     g = oracle.grid(crd, c, tabs, prm, threads=threads)
-    crd1 = oracle.coords(ob.uvw, ob.freqs, prm)
-    oracle.degrid(crd1, g, tabs, prm, threads=threads)
-    oracle.fft_to_image(g, max(oracle.sum_weights(ob.weight, crd), 1.0), prm)
+    t.append(time.perf_counter())
+    pred = oracle.degrid(crd1, g, tabs, prm, threads=threads)
+    t.append(time.perf_counter())
+    sw = max(oracle.sum_weights(sp.weight, crd), 1.0)
+    img = oracle.fft_to_image(g, sw, prm)
+    t.append(time.perf_counter())
+    names = ("wkernels", "coords", "grid", "degrid", "fft_image")
+    out = {"seconds": t[-1] - t[0], "phases_s": {k: round(t[i + 1] - t[i], 4) for i, k in enumerate(names)},
+           "kept": int(crd["keep"].sum()), "kept_degrid": int(crd1["keep"].sum())}
+    if keep:
+        out.update(tabs=tabs, crd=crd, crd1=crd1, c=c, grid=g, sum_w=sw, image=img, pred=pred)
+    return out
+
+
+def single_thread_grid_rate(sp: CpuSample, res, frac=16):
+    """The paper's single-thread figure (Sec. 3.1-3.2): the oracle's scatter on one thread, on
+    the first 1/frac of the sample's gridded visibilities."""
+    import oracle
+    crd = dict(res["crd"])
+    keep = crd["keep"].copy()
+    cut = np.zeros_like(keep)
+    cut[: max(1, keep.size // frac)] = True
+    crd["keep"] = keep & cut
+    n = int(crd["keep"].sum())
+    t0 = time.perf_counter()
+    oracle.grid(crd, res["c"], res["tabs"], sp.prm, threads=1)
     dt = time.perf_counter() - t0
-    kept = int(crd["keep"].sum())
-    return {"value": kept / dt, "unit": "visibilities/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {rows} rows ({kept} gridded visibilities) of the workload, full step "
-                      f"(kernels, coordinates, grid, degrid, image), float64, {dt:.1f} s on {threads} of {cores} cores",
-            "seconds": dt, "kept": kept}
+    return {"grid_vis_per_s": n / dt, "gridded_visibilities": n, "seconds": round(dt, 3), "threads": 1}
+
+
+def cpu_baseline(args, sp: CpuSample, keep=False):
+    """The float64 oracle on the host cores over the bounded sample `sp`: the same step as on
+    the GPU (kernels, coordinates, grid, degrid, image)."""
+    cores, threads = host_threads()
+    r = oracle_step(sp, threads, keep=keep)
+    dt = r["seconds"]
+    cb = {"value": r["kept"] / dt, "unit": "visibilities/s", "cores": threads, "kind": "oracle",
+          "sample": f"first {sp.rows} rows ({r['kept']} gridded visibilities) of the workload, full step "
+                    f"(kernels, coordinates, grid, degrid, image), float64, {dt:.1f} s on {threads} of {cores} cores",
+          "phases_s": r["phases_s"]}
+    return cb, r
+
+
+def peak_rel(a, ref):
+    a, ref = np.asarray(a), np.asarray(ref)
+    scale = float(np.abs(ref).max())
+    d = np.abs(a - ref)
+    return {"max": float(d.max() / scale), "rms": float(np.sqrt(np.mean(d ** 2)) / scale)}
+
+
+def error_figures(wp, sp: CpuSample, res):
+    """Peak-relative max and RMS error of the GPU path against the float64 oracle on the
+    sample: grid, uncorrected image (all pixels), corrected image (inner half, where the taper
+    is not near zero) and degridded visibilities (of the GPU's own grid, so that only the
+    degridding arithmetic differs)."""
+    import torch
+    import oracle
+    dev = torch.device("cuda", torch.cuda.current_device())
+    uvw = torch.from_numpy(np.ascontiguousarray(sp.uvw)).to(dev)
+    f = torch.from_numpy(np.ascontiguousarray(sp.freqs)).to(dev)
+    vis = torch.from_numpy(np.ascontiguousarray(sp.vis)).to(dev)
+    wt = torch.from_numpy(np.ascontiguousarray(sp.weight)).to(dev)
+    g, sw, _ = wp.grid(uvw, f, vis, wt, hermitian_pairs=sp.cfg.hermitian_pairs)
+    pred = wp.degrid(uvw, f, g)
+    g_host = g.cpu().numpy()
+    img_u = wp.fft_to_image(g.clone(), sw, taper_correct=False).cpu().numpy()
+    img_c = wp.fft_to_image(g, sw, taper_correct=True).cpu().numpy()
+    n = sp.prm.n
+    q = slice(n // 4, 3 * n // 4)
+    ref_u = oracle.fft_to_image(res["grid"], res["sum_w"], sp.prm, taper_correct=False)
+    ref_pred = oracle.degrid(res["crd1"], g_host.astype(np.complex128), res["tabs"], sp.prm, threads=host_threads()[1])
+    return {"grid": peak_rel(g_host, res["grid"]),
+            "image_uncorrected": peak_rel(img_u, ref_u),
+            "image_corrected_inner": peak_rel(img_c[q, q], res["image"][q, q]),
+            "degrid": peak_rel(pred.cpu().numpy().ravel(), ref_pred.ravel()),
+            "sample": f"first {sp.rows} rows of the workload ({res['kept']} gridded visibilities)"}
 
 
 def run_reference(args):
@@ -357,22 +534,23 @@ def run_reference(args):
     import synth
     cfg = synth.config(args.config)
     rows = cpu_sample_rows(cfg, args.cpu_vis)
-    times, cb = [], None
+    sp = cpu_sample_from_host(cfg, rows)        # inputs made once, outside the timing
+    cores, threads = host_threads()
+    times, r = [], None
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(args, rows=rows)
+        r = oracle_step(sp, threads)
         if i >= args.warmup:
             times.append(r["seconds"])
-            cb = r
     ms = 1e3 * float(np.mean(times))
-    value = cb["kept"] / (ms * 1e-3)
-    cb = dict(cb)
-    cb.pop("seconds")
-    cb.pop("kept")
-    cb["value"] = value
+    value = r["kept"] / (ms * 1e-3)
+    cb = {"value": value, "unit": "visibilities/s", "cores": threads, "kind": "oracle",
+          "sample": f"first {rows} rows ({r['kept']} gridded visibilities) of the workload per step, full step "
+                    f"(kernels, coordinates, grid, degrid, image), float64, on {threads} of {cores} cores",
+          "phases_s": r["phases_s"]}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "visibilities/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-            "config": {"workload": WORKLOAD, "sample_rows": rows}, "cpu_baseline": cb,
+            "config": {"workload": workload_name(args.config), "sample_rows": rows}, "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "visibilities/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -566,19 +744,25 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wproj", choices=["wproj", "reference"])
     ap.add_argument("--config", default="fp32",
-                    help="fp32 | mixed (imaging step), batched (many jobs), compare (the paper's GPU scheme)")
+                    help="fp32 | mixed | diff (imaging step), batched (many jobs), compare (the paper's GPU "
+                         "scheme), fp32peak (the FMA probe)")
     ap.add_argument("--table", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--tile", default="", help="origin tile WxH, e.g. 64x32")
     ap.add_argument("--cpu-vis", type=int, default=6_000_000, help="visibilities (rows x channels) in the CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-probe", action="store_true", help="skip the FP32 FMA probe")
+    ap.add_argument("--variants", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the f16/bf16 tables on the same workload, with their errors")
     ap.add_argument("--rows", type=int, default=0, help="use only the first ROWS rows (profiling captures)")
     ap.add_argument("--jobs", type=int, default=64, help="--config batched: number of jobs")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="--config batched: visibility-count scale")
     args = ap.parse_args()
     if args.impl != "reference":
         args.warmup = max(args.warmup, 3)
-    if args.config == "batched" and args.impl != "reference":
+    if args.config == "fp32peak" and args.impl != "reference":
+        out = run_fp32peak(args)
+    elif args.config == "batched" and args.impl != "reference":
         out = run_batched(args)
     elif args.config == "compare" and args.impl != "reference":
         out = run_compare(args)

@@ -14,6 +14,8 @@
  *     WP_ECUDA the context may hold partial results; other failures leave outputs untouched.
  *   - A context is not thread-safe and its scratch is shared by its calls: issue calls on
  *     one context from one host thread, on one stream at a time.
+ *   - Calls that take a context make the context's device current (cudaSetDevice) and leave
+ *     it current on return; they do not restore the caller's previous device.
  *   - Complex values are interleaved (re, im) float32 pairs ("float2"); arrays are C order.
  *   - Units: uvw in metres, frequencies in Hz, cell size in radians, w in wavelengths.
  *
@@ -126,9 +128,11 @@ int wp_grid(wp_ctx* ctx, const double* uvw, const double* freq, const void* vis,
  * message and touch nothing. The call allocates nothing: no cudaMalloc, no cudaFree, no
  * allocating library routine.
  *
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current) and caches it; make that first call before any stream capture.
- * All calls, from every context on the device, share the one array, and it keeps the last
+ * wp_create looks up the array's device address (cudaGetSymbolAddress, with the context's
+ * device current), which also loads the array on that device, and caches it per device, so
+ * this call itself neither loads nor looks up anything on a device that has a context. The
+ * cache does not survive cudaDeviceReset: contexts made before a reset are unusable after it,
+ * and the next wp_create on that device resolves the address again. All calls, from every context on the device, share the one array, and it keeps the last
  * call's contents (each call writes every record it reads, so nothing in it needs to start
  * at zero): calls that overlap on the GPU (different streams, or different contexts on the
  * same device, in flight at the same time) race on it and must be serialised by the caller.
@@ -289,6 +293,17 @@ int wp_profile(wp_ctx* ctx, int32_t enable);
  * and the number of this library's kernel launches since the last read; resets all three.
  * Any output pointer may be NULL. Synchronous. */
 int wp_profile_read(wp_ctx* ctx, double* ms_out, int32_t* count_out, int64_t* launches_out);
+
+/* Measurement aid (no counterpart in the paper): the device's FP32 FMA throughput, the
+ * compute bound of the gridding roofline (8 flop per kernel tap). Runs `reps` timed launches
+ * (after one warm-up launch) of a kernel whose threads each run 16 independent FMA chains of
+ * `iters` steps, as scalar fma.rn.f32 (packed == 0) or packed fma.rn.f32x2 (packed != 0, the
+ * form the gridding kernels issue), on every SM at full occupancy, on the legacy default
+ * stream. Writes TFLOP/s (2 flop per FMA) to *tflops_out and the mean launch time in ms to
+ * *ms_out (may be NULL). Synchronous; allocates 8 bytes of device memory for the duration.
+ * Errors: WP_EINVAL (iters or reps < 1, NULL tflops_out, no such device), WP_ECUDA. */
+int wp_probe_fp32_fma(int32_t device, int32_t packed, int64_t iters, int32_t reps, double* tflops_out,
+                      double* ms_out);
 
 /* Host only (no device needed): the taper t(x) = psi_0(c, x) / psi_0(c, 0) that
  * wp_make_wkernels and wp_fft_to_image use, at n points |x| <= 1 (host arrays).

@@ -19,7 +19,7 @@ SYMBOLS = ("wp_create", "wp_destroy", "wp_last_error", "wp_make_wkernels", "wp_g
            "wp_fft_to_image", "wp_plane_info", "wp_coords", "wp_wkernel_export", "wp_wkernel_norm",
            "wp_profile", "wp_profile_read", "wp_taper_eval_host", "wp_grid_noalloc", "wp_degrid_last", "wp_image_to_grid",
            "wp_batch_create", "wp_batch_grid", "wp_batch_fused_jobs", "wp_batch_destroy",
-           "wp_baseline_order", "wp_grid_baseline")
+           "wp_baseline_order", "wp_grid_baseline", "wp_probe_fp32_fma")
 PHASES = ("wkernels", "plan", "grid", "degrid", "fft", "image")
 
 
@@ -76,6 +76,7 @@ def _load():
     L.wp_profile_read.argtypes = [P, P, P, P]
     L.wp_taper_eval_host.argtypes = [D, P, I64, P]
     L.wp_grid_noalloc.argtypes = [P, P, P, P, P, I64, I32, I32, P, P, P, P]
+    L.wp_probe_fp32_fma.argtypes = [I32, I32, I64, I32, P, P]
     return L
 
 
@@ -90,6 +91,15 @@ def taper_eval_host(c: float, x) -> np.ndarray:
     if rc:
         raise WProjError(rc, "wp_taper_eval_host: invalid argument")
     return out
+
+
+def probe_fp32_fma(device: int = 0, packed: bool = True, iters: int = 100_000, reps: int = 5):
+    """Measured FP32 FMA throughput of the device: (TFLOP/s, ms per launch)."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = lib.wp_probe_fp32_fma(device, 1 if packed else 0, iters, reps, ctypes.byref(tf), ctypes.byref(ms))
+    if rc:
+        raise WProjError(rc, "wp_probe_fp32_fma failed")
+    return tf.value, ms.value
 
 
 def _ptr(t):

@@ -177,6 +177,8 @@ cudaError_t launch_grid_baseline(wp_ctx* ctx, const int32_t* coords, const uint3
                                  const float* weight, float2* grid, cudaStream_t s);
 cudaError_t launch_kept_sums(wp_ctx* ctx, const int32_t* coords, int64_t ng, int64_t nvis, const float* weight,
                              cudaStream_t s);
+// the fixed scratch of wp_grid_noalloc (noalloc.cu): resolve its address on `dev` (current)
+cudaError_t noalloc_prepare(int dev);
 // imaging (image.cu)
 cudaError_t launch_taper_inverse(const double* taper_img, float* inv, int32_t n, cudaStream_t s);
 cudaError_t launch_image_pre(const float* image, const double* sum_w, const float* inv_taper, int32_t taper_correct,

@@ -25,16 +25,30 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 std::mutex g_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_scratch on `dev` (which must be current). The first call per device
-// looks it up; later calls reuse it.
-cudaError_t scratch_address(int dev, void** out) {
+// Looks up the device address of g_scratch on `dev` (which must be current) and caches it.
+// The lookup also loads this file's module on that device, which is when the array's memory
+// is taken: wp_create does it, so that a wp_grid_noalloc call never loads the module itself.
+cudaError_t lookup_scratch(int dev) {
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess) return e;
+  g_scratch_addr[dev] = p;
+  return cudaSuccess;
+}
+
+// The cached address for `dev`, looked up now if no context has done it yet.
+cudaError_t scratch_address(int dev, void** out) {
+  {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (g_scratch_addr[dev]) {
+      *out = g_scratch_addr[dev];
+      return cudaSuccess;
+    }
   }
+  const cudaError_t e = lookup_scratch(dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_mutex);
   *out = g_scratch_addr[dev];
   return cudaSuccess;
 }
@@ -70,6 +84,16 @@ struct ScratchView {
 };
 
 }  // namespace
+
+namespace wp {
+// Called by wp_create with the context's device current: resolves (again) the scratch array's
+// address on that device. Re-resolving at every context creation keeps the cache valid after a
+// cudaDeviceReset, since contexts made before a reset cannot be used after it anyway.
+cudaError_t noalloc_prepare(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return cudaSuccess;     // wp_grid_noalloc rejects such devices
+  return lookup_scratch(dev);
+}
+}  // namespace wp
 
 extern "C" int wp_grid_noalloc(wp_ctx* ctx, const double* uvw, const double* freq, const void* vis,
                                const float* weight, int64_t nrow, int32_t nchan, int32_t flags, void* grid,

@@ -238,6 +238,8 @@ int wp_create(wp_ctx** out, const wp_params* p) {
     return code;
   };
   if (cudaSetDevice(q.device) != cudaSuccess) return bail(WP_ECUDA, "cudaSetDevice failed");
+  // the fixed scratch of wp_grid_noalloc is taken here, not inside that call
+  if (wp::noalloc_prepare(q.device) != cudaSuccess) return bail(WP_ECUDA, "wp_grid_noalloc scratch set-up failed");
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, q.device) != cudaSuccess) return bail(WP_ECUDA, "cudaGetDeviceProperties failed");
   ctx->nsm = prop.multiProcessorCount;

@@ -19,19 +19,33 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
-def _noalloc(wp, uvw, f, vis, wt, pairs=False):
+def _outputs(n):
     import torch
-    import paper_1905_03213_b300 as W
-    n = wp.n
     g = torch.full((n, n), 7.0 + 3.0j, dtype=torch.complex64, device="cuda")   # must be overwritten
     sw = torch.zeros(1, dtype=torch.float64, device="cuda")
     nd = torch.zeros(1, dtype=torch.int64, device="cuda")
-    flags = W.WP_HERMITIAN_PAIRS if pairs else 0
+    return g, sw, nd
+
+
+def _call(wp, uvw, f, vis, wt, out, pairs=False, accumulate=False):
+    """wp_grid_noalloc through the C ABI into preallocated outputs; no host-side allocation of
+    device memory happens here either."""
+    import torch
+    import paper_1905_03213_b300 as W
+    g, sw, nd = out
+    flags = (W.WP_HERMITIAN_PAIRS if pairs else 0) | (W.WP_ACCUMULATE if accumulate else 0)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = W.lib.wp_grid_noalloc(wp._h, _ptr(uvw), _ptr(f), _ptr(vis), _ptr(wt), uvw.shape[0], f.shape[0], flags,
                                _ptr(g), _ptr(sw), _ptr(nd), stream)
     assert rc == 0, W.lib.wp_last_error(wp._h).decode()
+
+
+def _noalloc(wp, uvw, f, vis, wt, pairs=False):
+    import torch
+    out = _outputs(wp.n)
+    _call(wp, uvw, f, vis, wt, out, pairs=pairs)
     torch.cuda.synchronize()
+    g, sw, nd = out
     return g.cpu().numpy(), sw.item(), nd.item()
 
 
@@ -72,3 +86,41 @@ def test_noalloc_rejects_calls_beyond_its_scratch():
     assert rc == W._abi.WP_EINVAL
     assert b"1048576" in W.lib.wp_last_error(wp._h)
     assert torch.count_nonzero(g).item() == 0
+
+
+def test_noalloc_first_call_on_a_fresh_context_allocates_nothing():
+    """A context that has never run wp_grid holds no coordinate scratch, so this call takes the
+    path that recomputes the coordinates in the scatter pass. Across the call (after one
+    warm-up call on another context has loaded the kernels), neither the device's free memory
+    nor torch's reserved pool changes. Supports 6-10 (not only 7), several channels, weights,
+    then an accumulating second call; the reference is wp_grid on a separate context."""
+    import torch
+    case = random_case(n=128, nrow=3000, nchan=3, n_w=6, s_min=6, s_max=10, seed=23)
+    uvw, f, vis, wt = to_dev(case)
+    warm = make_wproj(case)
+    _noalloc(warm, uvw, f, vis, wt)                     # loads every kernel of the path
+    ref = make_wproj(case)
+    g_ref, sw_ref, nd_ref = ref.grid(uvw, f, vis, wt)
+    g_ref2, sw_ref2, nd_ref2 = ref.grid(uvw[:1234].contiguous(), f, vis[:1234].contiguous(), wt[:1234].contiguous(),
+                                        grid=g_ref.clone(), sum_w=sw_ref.clone(), n_dropped=nd_ref.clone(),
+                                        accumulate=True)
+    fresh = make_wproj(case)
+    out = _outputs(fresh.n)
+    uvw2, vis2, wt2 = uvw[:1234].contiguous(), vis[:1234].contiguous(), wt[:1234].contiguous()
+    torch.cuda.synchronize()
+    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    _call(fresh, uvw, f, vis, wt, out)
+    torch.cuda.synchronize()
+    free1, reserved1 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    assert (free1, reserved1) == (free0, reserved0), (free0 - free1, reserved1 - reserved0)
+    g, sw, nd = out
+    e1, _ = peak_rel(g.cpu().numpy(), g_ref.cpu().numpy())
+    assert e1 < 1e-6, e1
+    assert sw.item() == pytest.approx(sw_ref.item(), rel=1e-12) and nd.item() == nd_ref.item()
+    # second call in a row, accumulating a ragged slice onto the first result
+    _call(fresh, uvw2, f, vis2, wt2, out, accumulate=True)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    e2, _ = peak_rel(g.cpu().numpy(), g_ref2.cpu().numpy())
+    assert e2 < 1e-6, e2
+    assert sw.item() == pytest.approx(sw_ref2.item(), rel=1e-12) and nd.item() == nd_ref2.item()
