@@ -39,7 +39,14 @@ extern "C" {
 #define WP_EOVERFLOW 4   /* a size exceeds a 32-bit index the kernels use */
 #define WP_ESTATE    5   /* call order: e.g. gridding before wp_make_wkernels */
 
-/* Kernel-table precision (stored precision; generation is always float64). */
+/* Kernel-table precision (stored precision; generation is always float64). The gridding
+ * arithmetic is float32 for every table type; only the stored taps are rounded.
+ *   WP_TABLE_F32  float32 (re, im) pairs, 8 bytes per tap.
+ *   WP_TABLE_F16  float16 (re, im) pairs, 4 bytes per tap.
+ *   WP_TABLE_BF16 one 32-bit word w per tap, 4 bytes: re = (w << 16) read as float32 (re rounded
+ *                 to bfloat16), im = w read as float32 (the float32 nearest to im among those whose
+ *                 low 16 bits are re's bits). Both within half a bfloat16 ulp; a kernel widens a
+ *                 tap to float32 with one shift. */
 #define WP_TABLE_F32  0
 #define WP_TABLE_F16  1
 #define WP_TABLE_BF16 2
@@ -120,9 +127,10 @@ int wp_grid(wp_ctx* ctx, const double* uvw, const double* freq, const void* vis,
  * kernels once beforehand (wp_create and wp_make_wkernels do allocate) and then calls this.
  *
  * Same arguments, flags, results and errors as wp_grid, computed by the same kernels. The
- * per-call scratch that wp_grid keeps in a growable context buffer (one 16-byte record per
- * gridded visibility, plus per-channel factors) is instead a fixed file-scope device array
- * of 16 MiB + 64 KiB, which every GPU that loads this library holds until the process exits.
+ * per-call scratch that wp_grid keeps in growable context buffers (two 16-byte records per
+ * gridded visibility: binned, then sorted by footprint origin; plus per-channel factors) is
+ * instead a fixed file-scope device array of 32 MiB + 64 KiB, which every GPU that loads this
+ * library holds until the process exits.
  * Limits: at most 2^20 = 1048576 gridded visibilities per call (nrow * nchan, doubled with
  * WP_HERMITIAN_PAIRS) and at most 4096 channels; larger calls return WP_EINVAL with a
  * message and touch nothing. The call allocates nothing: no cudaMalloc, no cudaFree, no

@@ -136,8 +136,9 @@ __device__ __forceinline__ float2 tap_f2<__half2>(const __half2* p) {
   return __half22float2(__ldg(p));
 }
 template <>
-__device__ __forceinline__ float2 tap_f2<__nv_bfloat162>(const __nv_bfloat162* p) {
-  return __bfloat1622float2(__ldg(p));
+__device__ __forceinline__ float2 tap_f2<BfWord>(const BfWord* p) {
+  const uint32_t w = __ldg((const unsigned int*)p);
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w));
 }
 
 // One CTA per (baseline b, channel ch, partner h); thread (ta, tb) = tap column ta, row tb of
@@ -263,8 +264,8 @@ cudaError_t launch_grid_baseline(wp_ctx* ctx, const int32_t* coords, const uint3
                                                                      ctx->d_tab_off, grid);
       break;
     case WP_TABLE_BF16:
-      k_grid_baseline<__nv_bfloat162><<<(unsigned)nblocks, threads, 0, s>>>(
-          coords, start, perm, nb, nchan, nvis, smax, vis, weight, ctx->geo, (const __nv_bfloat162*)ctx->d_tab,
+      k_grid_baseline<BfWord><<<(unsigned)nblocks, threads, 0, s>>>(
+          coords, start, perm, nb, nchan, nvis, smax, vis, weight, ctx->geo, (const BfWord*)ctx->d_tab,
           ctx->d_tab_off, grid);
       break;
     default:

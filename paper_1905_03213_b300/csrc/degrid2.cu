@@ -57,10 +57,12 @@ __host__ __device__ constexpr int sub_bytes(int tile_x, int tile_y, int group, i
 // records; on return v[0] of lane l is the warp total of record l mod NB.
 template <int NB>
 __device__ __forceinline__ void batch_reduce(float (&v)[NB], int lane) {
-  int n = NB;
-  if (NB == 16) {
+  static_assert(NB == 8 || NB == 16 || NB == 32, "batch of 8, 16 or 32 records");
+  // lanes l and l ^ off hold partials of the same records: add them first
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 16);
+  for (int off = 16; off >= NB; off >>= 1) {
+#pragma unroll
+    for (int i = 0; i < NB; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
   }
 #pragma unroll
   for (int bit = NB / 2; bit >= 1; bit >>= 1) {
@@ -72,30 +74,35 @@ __device__ __forceinline__ void batch_reduce(float (&v)[NB], int lane) {
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
     }
   }
-  (void)n;
 }
 
 // One warp degrids the decoded, sorted records [beg, end) of the chunk at byte offset rec_off
 // from the grid region staged at sub_off (pitch entries per row, origin (sx0, sy0)). Table as
-// in the gridding kernel (staged at tab_off, or the global copy gtab for S > 16, row half h);
-// with two row halves each warp adds its half of every visibility to the (zeroed) output.
+// in the gridding kernel (tap layout staged at tab_off, or the global copy gtab for S > 16,
+// row half h); with two row halves each warp adds its half of every visibility to the
+// (zeroed) output. Decoded record: x = output index, y = s as float bits (+1 for K_k = K_p,
+// -1 for K_k = conj K_p), z = origin i0 | j0 << 16, w = class byte offset in the table.
+//
+// Per record a lane forms, over its rows, with the tap pair (kr, ki) and its cell (gr, gi)
+// (held as the pairs (gr, gi) and (gi, gr)):
+//   P1 += (kr, ki) * (gr, gi),  P2 += (kr, ki) * (gi, gr)
+// and its part of conj(K_k) G is (P1.x + s P1.y) + i (P2.x - s P2.y).
 template <int S, class T, bool kGlobal>
 __device__ __forceinline__ void warp_degrid(int tab_off, const unsigned char* gtab, int h, int sub_off, int pitch,
                                             int sx0, int sy0, int rec_off, int beg, int end,
                                             float2* __restrict__ out) {
   using L = Lay<S, T>;
-  constexpr int NB = L::RP <= 2 ? 32 : 16;
+  constexpr int NB = L::R <= 5 ? 32 : (L::R <= 8 ? 16 : 8);
   const int lane = threadIdx.x & 31;
-  const int g = lane / S, a = lane - g * S;
+  const int g = lane / S, slot = lane - g * S;
   // lanes beyond the layout read (zero-tap) cells of the half's first row
   const int row0 = L::H > 1 ? h * L::R : (lane < L::NL ? g * L::R : 0);
-  const unsigned char* tab = (kGlobal ? gtab : dyn_smem() + tab_off) + h * L::HB;
+  const unsigned char* lt = (kGlobal ? gtab : dyn_smem() + tab_off) + h * L::HB + lane * L::SB;
   const float2* sub = (const float2*)(dyn_smem() + sub_off);
   const uint4* drec = (const uint4*)(dyn_smem() + rec_off);
-  unsigned long long GR[L::RPA], GI[L::RPA], NGI[L::RPA];   // cells: re, im, -im of row pairs
-  float gtr = 0.f, gti = 0.f;
+  unsigned long long GA[L::R], GB[L::R];      // cells (gr, gi) and (gi, gr) of this lane's rows
 #pragma unroll
-  for (int k = 0; k < L::RPA; ++k) GR[k] = GI[k] = NGI[k] = 0ull;
+  for (int k = 0; k < L::R; ++k) GA[k] = GB[k] = 0ull;
   uint32_t cz = kNoOrigin;
   for (int b0 = beg; b0 < end; b0 += NB) {
     float pre[NB], pim[NB];
@@ -104,45 +111,27 @@ __device__ __forceinline__ void warp_degrid(int tab_off, const unsigned char* gt
       pre[r] = pim[r] = 0.f;
       if (b0 + r < end) {                          // warp-uniform
         const uint4 rec = drec[b0 + r];
-        Taps<S, T, kGlobal> tv;
-        tv.load(tab + (rec.w & 0x7fffffffu), lane);
         if (rec.z != cz) {                         // warp-uniform: load the cells under the new origin
           cz = rec.z;
-          const float2* c = sub + ((int)(rec.z >> 16) - sy0 + row0) * pitch + ((int)(rec.z & 0xffff) - sx0) + a;
+          const float2* c = sub + ((int)(rec.z >> 16) - sy0 + row0) * pitch + ((int)(rec.z & 0xffff) - sx0) + slot;
 #pragma unroll
-          for (int k = 0; k < L::RP; ++k) {
-            const float2 c0 = c[(2 * k) * pitch], c1 = c[(2 * k + 1) * pitch];
-            GR[k] = pack2(c0.x, c1.x);
-            GI[k] = pack2(c0.y, c1.y);
-            NGI[k] = pack2(-c0.y, -c1.y);
-          }
-          if (L::RT) {
-            const float2 ct = c[(2 * L::RP) * pitch];
-            gtr = ct.x;
-            gti = ct.y;
+          for (int k = 0; k < L::R; ++k) {
+            const float2 v = c[k * pitch];
+            GA[k] = pack2(v.x, v.y);
+            GB[k] = pack2(v.y, v.x);
           }
         }
-        // conj(K_k) = (kr, -ki) for w >= 0 and (kr, ki) for w < 0: ki' = sg ki
-        const float sg = (rec.w & 0x80000000u) ? 1.f : -1.f;
-        const unsigned long long SG = pack2(sg, sg);
-        unsigned long long PR = 0ull, PI = 0ull;
+        const unsigned char* p = lt + rec.w;
+        unsigned long long P1 = 0ull, P2 = 0ull;
 #pragma unroll
-        for (int k = 0; k < L::RP; ++k) {
-          const unsigned long long kr = tv.r[k];
-          const unsigned long long ki = fma2(tv.i[k], SG, 0ull);
-          PR = fma2(kr, GR[k], PR);                // re: gr kr - gi ki'
-          PR = fma2(ki, NGI[k], PR);
-          PI = fma2(ki, GR[k], PI);                // im: gr ki' + gi kr
-          PI = fma2(kr, GI[k], PI);
+        for (int k = 0; k < L::R; ++k) {
+          const unsigned long long t = tap_pair<T, kGlobal>(p + k * L::BB);
+          P1 = fma2(t, GA[k], P1);
+          P2 = fma2(t, GB[k], P2);
         }
-        float sr = lo_of(PR) + hi_of(PR), si = lo_of(PI) + hi_of(PI);
-        if (L::RT) {
-          const float kt = sg * tv.ti;
-          sr = fmaf(gtr, tv.tr, fmaf(-gti, kt, sr));
-          si = fmaf(gtr, kt, fmaf(gti, tv.tr, si));
-        }
-        pre[r] = sr;
-        pim[r] = si;
+        const float sg = __uint_as_float(rec.y);
+        pre[r] = fmaf(sg, hi_of(P1), lo_of(P1));
+        pim[r] = fmaf(-sg, hi_of(P2), lo_of(P2));
       }
     }
     batch_reduce<NB>(pre, lane);
@@ -172,9 +161,17 @@ __device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, 
   }
   const int keys = width * a.g.tile_y;
   const int warp = threadIdx.x >> 5;
+  const int os = a.g.os;
+  uint4* drec = (uint4*)(dyn_smem() + rec_off);
+  const bool indexed = a.index != nullptr;
   for (uint32_t c0 = s0; c0 < s1; c0 += (uint32_t)cap) {
     const int m = (int)min((uint32_t)cap, s1 - c0);
-    const int kept = sort_chunk<S, T>((const uint4*)a.recs, a.index, c0, m, x0, y0, width, keys, a.g.os, rec_off);
+    const int kept = sort_chunk((const uint4*)a.recs, a.index, c0, m, x0, y0, width, keys,
+                                [&](int slot, const uint4& rec, uint32_t idx) {
+      const int cls = (int)((rec.w >> 8) & 0xff) * os + (int)(rec.w & 0xff);
+      const uint32_t sg = (rec.w & 0x80000000u) ? 0xbf800000u : 0x3f800000u;     // -1.0f or +1.0f
+      drec[slot] = make_uint4(indexed ? idx : rec.x, sg, rec.z, (uint32_t)(cls * L::CB));
+    });
     const int piece = warp / L::H, h = warp % L::H;
     const int beg = (int)((int64_t)kept * piece / kPieces), end = (int)((int64_t)kept * (piece + 1) / kPieces);
     if (L::H == 1 || staged) warp_degrid<S, T, false>(tab_off, nullptr, h, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
@@ -298,7 +295,7 @@ cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* out, const
   };
   switch (ctx->prm.table_type) {
     case WP_TABLE_F16: return run(k_degrid_v2<__half2>);
-    case WP_TABLE_BF16: return run(k_degrid_v2<__nv_bfloat162>);
+    case WP_TABLE_BF16: return run(k_degrid_v2<BfWord>);
     default: return run(k_degrid_v2<float2>);
   }
 }

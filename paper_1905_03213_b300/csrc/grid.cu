@@ -35,8 +35,9 @@ __device__ __forceinline__ float2 load_tap<__half2>(const __half2* p) {
   return __half22float2(__ldg(p));
 }
 template <>
-__device__ __forceinline__ float2 load_tap<__nv_bfloat162>(const __nv_bfloat162* p) {
-  return __bfloat1622float2(__ldg(p));
+__device__ __forceinline__ float2 load_tap<BfWord>(const BfWord* p) {
+  const uint32_t w = __ldg((const unsigned int*)p);
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w));
 }
 
 struct TableRef {
@@ -207,7 +208,7 @@ cudaError_t launch_grid(wp_ctx* ctx, float2* grid, cudaStream_t s) {
   if (e != cudaSuccess || used) return e;
   switch (ctx->prm.table_type) {
     case WP_TABLE_F16: return grid_typed<__half2>(ctx, grid, s);
-    case WP_TABLE_BF16: return grid_typed<__nv_bfloat162>(ctx, grid, s);
+    case WP_TABLE_BF16: return grid_typed<BfWord>(ctx, grid, s);
     default: return grid_typed<float2>(ctx, grid, s);
   }
 }
@@ -219,7 +220,7 @@ cudaError_t launch_degrid(wp_ctx* ctx, const float2* grid, float2* out, const ui
   if (e != cudaSuccess || used) return e;
   switch (ctx->prm.table_type) {
     case WP_TABLE_F16: return degrid_typed<__half2>(ctx, grid, out, index, s);
-    case WP_TABLE_BF16: return degrid_typed<__nv_bfloat162>(ctx, grid, out, index, s);
+    case WP_TABLE_BF16: return degrid_typed<BfWord>(ctx, grid, out, index, s);
     default: return degrid_typed<float2>(ctx, grid, out, index, s);
   }
 }

@@ -3,24 +3,21 @@
 // Gridding (Sec. 2.1/2.2 of Lao et al. 2019): visibility k adds c_k K_k(a, b) to the cell
 // (i0 + a, j0 + b) of its S x S footprint. The paper's GPU scheme (Fig. 2, after Romein)
 // keeps each support tap's running sum in a register while the grid point it maps to stays
-// the same; here that idea is organised around sorted bins and whole warps:
+// the same; here that idea is organised around records sorted by (w-plane, origin tile,
+// footprint origin) and whole warps:
 //
-//   * A CTA takes a contiguous share of the (plane, tile)-sorted records, of equal estimated
-//     work, and counting-sorts each chunk of them by footprint origin (row j0, then column
-//     i0) in shared memory; the chunk is as large as the shared memory left beside the
-//     plane's staged table.
-//   * Each warp walks one contiguous piece of the sorted chunk, all 32 lanes on the same
-//     record, so every branch is warp-uniform. Lane (g, a) holds rows g R .. g R + R - 1 of
-//     footprint column a in registers (row pairs packed for f32x2 FMAs): the warp's
-//     registers are the S x S cells under the current origin.
-//   * Consecutive records with the same origin accumulate in place. When the origin moves
-//     right by d < S columns on the same row, the lanes of the d leaving columns add their
-//     cells to the HBM grid (vector reductions) and the accumulators slide d lanes with one
-//     shuffle per register; any other move flushes all S x S cells. Per record and row pair a
-//     lane does two 8-byte table loads (the kr and ki pairs, each a 256-byte conflict-free
-//     block per warp) and four packed FMAs.
-//   * CTAs take work units (equal shares of the estimated work) from a global counter, the
-//     most expensive end of the record order first, so no CTA is left with a long tail.
+//   * The plan sorts each (plane, tile) bin's records by footprint origin (row j0, then column
+//     i0), so the records of one origin are contiguous. A CTA takes work units (shares of the
+//     estimated work) from a global counter, the most expensive end first; per plane inside a
+//     unit it stages the plane's table in shared memory and gives each warp one contiguous
+//     piece of the plane's records. There is no other CTA-wide step.
+//   * A warp streams its piece 32 records at a time: each lane loads one record (coalesced),
+//     decodes it into the warp's shared-memory ring (FMA operands, origin, class offset), and
+//     loads its record of the next group while the warp walks this one.
+//   * The walk: all 32 lanes on the same record, so every branch is warp-uniform. Lane (g, a)
+//     holds rows g R .. g R + R - 1 of one footprint column in registers: the warp's registers
+//     are the S x S cells under the current origin. Records of the same origin accumulate in
+//     place; footprint moves are described at warp_grid.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,160 +47,230 @@ struct G2Args {
   uint32_t* work;           // [2]: next unit, finished CTAs (both zero between launches)
 };
 
-// The S x S cells under one footprint origin, distributed over a warp (see Lay).
+// The warp's ring in shared memory: 32 decoded records, the FMA operands (cr, be, ci, de) and
+// the header (origin i0 | j0 << 16, byte offset of the record's class in the plane's table).
+constexpr int kRingRecs = 64;                  // a group: two records per lane
+constexpr int kRingBytes = kRingRecs * (16 + 8);
+constexpr int kRingsBytes = kWarps * kRingBytes;
+constexpr uint32_t kBatch = 256;               // records a warp takes at a time (S <= 16)
+
+// The S x S cells under one footprint origin, distributed over a warp (see Lay): lane row r
+// of this lane's footprint column, as two float32 pairs whose lane sums are the cell's real
+// and imaginary parts.
 template <int S>
 struct Footprint {
   using L = Lay<S>;
-  unsigned long long re[L::RPA], im[L::RPA];   // row pairs (2k, 2k + 1) of this lane's rows
-  float tre, tim;                              // tail row 2 RP
+  unsigned long long p1[L::R], p2[L::R];     // (cr kr, be ki) and (ci kr, de ki) summed over records
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int k = 0; k < L::RPA; ++k) re[k] = im[k] = 0ull;
-    tre = tim = 0.f;
+    for (int r = 0; r < L::R; ++r) p1[r] = p2[r] = 0ull;
+  }
+  // keep == false: zero (a select, so that a non-finite sum does not outlive its cell)
+  __device__ __forceinline__ void keep_if(bool keep) {
+#pragma unroll
+    for (int r = 0; r < L::R; ++r) {
+      p1[r] = keep ? p1[r] : 0ull;
+      p2[r] = keep ? p2[r] : 0ull;
+    }
   }
   // Adds this lane's cells to the grid where `pred`: rows r < nrow of its column, the first at
   // cell index idx (32-bit: n <= 32768), the next ones n cells apart. Predicated, no branch.
   __device__ __forceinline__ void flush(bool pred, float2* __restrict__ grid, uint32_t idx, uint32_t n, int nrow) const {
 #pragma unroll
-    for (int k = 0; k < L::RP; ++k) {
-      red_add2_if(pred && 2 * k < nrow, grid + idx, lo_of(re[k]), lo_of(im[k]));
+    for (int r = 0; r < L::R; ++r) {
+      red_add2_if(pred && r < nrow, grid + idx, lo_of(p1[r]) + hi_of(p1[r]), lo_of(p2[r]) + hi_of(p2[r]));
       idx += n;
-      red_add2_if(pred && 2 * k + 1 < nrow, grid + idx, hi_of(re[k]), hi_of(im[k]));
-      idx += n;
-    }
-    if (L::RT) red_add2_if(pred && 2 * L::RP < nrow, grid + idx, tre, tim);
-  }
-  // acc(a) <- acc(a + d); columns a + d >= S start at zero.
-  __device__ __forceinline__ void slide(int d, int a) {
-    const bool keep = a + d < S;
-#pragma unroll
-    for (int k = 0; k < L::RP; ++k) {
-      const unsigned long long r = shfl_down2(re[k], d), i = shfl_down2(im[k], d);
-      re[k] = keep ? r : 0ull;
-      im[k] = keep ? i : 0ull;
-    }
-    if (L::RT) {
-      const float r = __shfl_down_sync(0xffffffffu, tre, d), i = __shfl_down_sync(0xffffffffu, tim, d);
-      tre = keep ? r : 0.f;
-      tim = keep ? i : 0.f;
     }
   }
 };
 
-// One warp grids the decoded, sorted records [beg, end) of the chunk at byte offset rec_off.
-// Table: staged in shared memory at byte offset tab_off, or (kGlobal: S > 16 and too large to
-// stage beside a chunk) the plane's lane-order copy at gtab; per class Lay<S, T>::CB bytes as
-// described at Lay. Row half h (S > 16).
-// Decoded record: x, y = c (float bits); z = i0 | j0 << 16; w = class byte offset | conj << 31.
-// Taps are widened to float32; every product and sum is float32.
+// One warp grids the records [beg, end) of one plane (support S, table type T). Table: the
+// plane's tap layout in shared memory at tab_off, or (kGlobal: too large to stage) its global
+// copy gtab; row half h (S > 16). The records stream through the warp's ring at ring_off.
+//
+// Per record and tap, with the tap's pair (kr, ki):
+//   p1 += (cr, be) * (kr, ki),  p2 += (ci, de) * (kr, ki)    (two fma.rn.f32x2)
+// and the cell receives (p1.x + p1.y, p2.x + p2.y): c K with be = -ci, de = cr, or
+// c conj(K) (w < 0) with be = ci, de = -cr. Every product and sum is float32.
+//
+// Footprint moves (the paper's register reuse, Fig. 2, after Romein): lane slot a owns the
+// cells whose column is congruent to a modulo S. When the origin moves right by 0 < d < S on
+// the same row, a lane whose current tap column ac is >= d keeps its cells (now tap column
+// ac - d); the others add their cells to the grid and start on the column S cells further
+// right (tap column ac - d + S). So a slide moves no data between lanes; any other move
+// flushes every cell and resets ac to the lane's slot.
+// Loads this lane's two records of the group at q (records q + lane and q + 32 + lane below e).
+__device__ __forceinline__ void load_group(const uint4* __restrict__ grecs, uint32_t q, uint32_t e, int lane,
+                                           uint4& r0, uint4& r1) {
+  if (q + lane < e) r0 = __ldcs(grecs + q + lane);
+  if (q + 32 + lane < e) r1 = __ldcs(grecs + q + 32 + lane);
+}
+
+// The record's FMA operands and header in the ring: be = -ci, de = cr (K) or be = ci, de = -cr
+// (conj K), and the byte offset of its class in the plane's table.
+template <int CB>
+__device__ __forceinline__ void decode_record(const uint4& r, int os, ulonglong2* ops, uint2* hdr, int i) {
+  const uint32_t flip = (r.w & 0x80000000u) ^ 0x80000000u;      // sign bit set unless conj
+  ops[i] = make_ulonglong2((unsigned long long)r.x | ((unsigned long long)(r.y ^ flip) << 32),
+                           (unsigned long long)r.y | ((unsigned long long)(r.x ^ flip ^ 0x80000000u) << 32));
+  const uint32_t cls = ((r.w >> 8) & 0xffu) * (uint32_t)os + (r.w & 0xffu);
+  hdr[i] = make_uint2(r.z, cls * (uint32_t)CB);
+}
+
 template <int S, class T, bool kGlobal>
-__device__ __forceinline__ void warp_grid(int tab_off, const unsigned char* gtab, int h, int rec_off, int beg,
-                                          int end, float2* __restrict__ grid, int n) {
+__device__ __forceinline__ void warp_grid(const G2Args& a, int tab_off, const unsigned char* gtab, int h, int ring_off,
+                                          uint32_t pe, uint32_t* next, uint32_t sbeg, uint32_t send) {
   using L = Lay<S, T>;
   const int lane = threadIdx.x & 31;
-  const int g = lane / S, a = lane - g * S;
+  const int g = lane / S, slot = lane - g * S;
   const bool active = lane < L::NL;
   const int row0 = L::H > 1 ? h * L::R : g * L::R;
   const unsigned char* tab = (kGlobal ? gtab : dyn_smem() + tab_off) + h * L::HB;
-  const uint4* drec = (const uint4*)(dyn_smem() + rec_off);
+  ulonglong2* ops = (ulonglong2*)(dyn_smem() + ring_off);
+  uint2* hdr = (uint2*)(dyn_smem() + ring_off + 16 * kRingRecs);
+  const uint4* grecs = (const uint4*)a.recs;
+  float2* __restrict__ grid = a.grid;
+  const uint32_t n = (uint32_t)a.g.n;
+  const int os = a.g.os;
+  // batches: taken from the CTA's counter (next != nullptr), or the one static piece
+  auto grab = [&](uint32_t& b, uint32_t& e) {
+    if (next) {
+      uint32_t v = 0;
+      if (lane == 0) v = atomicAdd(next, kBatch);
+      b = __shfl_sync(0xffffffffu, v, 0);
+      e = b < pe ? min(b + kBatch, pe) : b;
+    } else {
+      b = sbeg;
+      e = send;
+      sbeg = send;
+    }
+  };
+  uint32_t cb, ce, nb, ne;
+  grab(cb, ce);
+  if (cb >= ce) return;
+  grab(nb, ne);
   Footprint<S> fp;
   fp.zero();
   uint32_t cz = kNoOrigin;
-  int col0 = 0, cj = 0;
-  // this lane's rows inside the footprint, and its offset from the origin's cell index
-  const int nrow = active ? min(L::R, S - row0) : 0;
-  const uint32_t lane_off = (uint32_t)row0 * (uint32_t)n + (uint32_t)a;
-  uint32_t cidx = 0;                               // cell index of this lane's first cell
-#pragma unroll(L::RP > 1 ? 2 : 4)
-  for (int q = beg; q < end; ++q) {
-    const uint4 rec = drec[q];
-    Taps<S, T, kGlobal> tv;
-    tv.load(tab + (rec.w & 0x7fffffffu), lane);
-    if (rec.z != cz) {                             // warp-uniform: a new footprint origin
-      const int i0 = rec.z & 0xffff, j0 = rec.z >> 16;
-      const int d = i0 - col0;
-      const bool slide = j0 == cj && (unsigned)(d - 1) < (unsigned)(S - 1);   // 0 < d < S on the same row
-      // a slide adds the d leaving columns to the grid, any other move every cell
-      fp.flush(cz != kNoOrigin && (!slide || a < d), grid, cidx, (uint32_t)n, nrow);
-      if (slide) fp.slide(d, a);
-      else fp.zero();
-      cz = rec.z;
-      col0 = i0;
-      cj = j0;
-      cidx = (uint32_t)j0 * (uint32_t)n + (uint32_t)i0 + lane_off;
-    }
-    // acc.re += cr kr + be ki, acc.im += ci kr + de ki: c K, or c conj(K) for w < 0
-    const uint32_t flip = (rec.w & 0x80000000u) ^ 0x80000000u;
-    const float cr = __uint_as_float(rec.x), cim = __uint_as_float(rec.y);
-    const float be = __uint_as_float(rec.y ^ flip), de = __uint_as_float(rec.x ^ flip ^ 0x80000000u);
-    const unsigned long long CR = pack2(cr, cr), CI = pack2(cim, cim);
-    const unsigned long long BE = pack2(be, be), DE = pack2(de, de);
+  int ci0 = 0, cj0 = -1;                                   // no row: the first origin never slides
+  const int nrow = active ? min(L::R, S - row0) : 0;       // this lane's rows inside the footprint
+  int ac = active ? slot : 0;                              // current tap column
+  const unsigned char* lt = tab + lane * L::SB;            // this lane's slot in each block
+  uint32_t cidx = 0;                                       // cell index of this lane's first cell
+  uint4 r0 = make_uint4(0u, 0u, 0u, 0u), r1 = r0;
+  uint32_t q = cb;
+  load_group(grecs, q, ce, lane, r0, r1);
+  for (;;) {
+    const int m = (int)min((uint32_t)kRingRecs, ce - q);
+    __syncwarp();
+    if (lane < m) decode_record<L::CB>(r0, os, ops, hdr, lane);
+    if (lane + 32 < m) decode_record<L::CB>(r1, os, ops, hdr, lane + 32);
+    __syncwarp();
+    // the next group (of this batch or of the next one) loads while the warp walks this one
+    const bool last = q + kRingRecs >= ce;
+    if (!last) load_group(grecs, q + kRingRecs, ce, lane, r0, r1);
+    else if (nb < ne) load_group(grecs, nb, ne, lane, r0, r1);
+#pragma unroll(L::R > 4 ? 1 : 2)
+    for (int j = 0; j < m; ++j) {
+      const uint2 hd = hdr[j];
+      const ulonglong2 op = ops[j];
+      if (hd.x != cz) {                                    // warp-uniform: a new footprint origin
+        const int i0 = hd.x & 0xffff, j0 = hd.x >> 16;
+        const int d = i0 - ci0;
+        const bool slide = j0 == cj0 && (unsigned)(d - 1) < (unsigned)(S - 1);   // 0 < d < S on the same row
+        const bool keep = slide && ac >= d;
+        fp.flush(cz != kNoOrigin && !keep, grid, cidx, n, nrow);
+        if (slide) {
+          fp.keep_if(keep);
+          ac = keep ? ac - d : ac - d + S;
+          cidx = keep ? cidx : cidx + S;
+        } else {
+          fp.zero();
+          ac = active ? slot : 0;
+          cidx = (uint32_t)(j0 + row0) * n + (uint32_t)(i0 + ac);
+        }
+        lt = tab + (active ? g * S + ac : lane) * L::SB;
+        cz = hd.x;
+        ci0 = i0;
+        cj0 = j0;
+      }
+      const unsigned char* p = lt + hd.y;
 #pragma unroll
-    for (int k = 0; k < L::RP; ++k) {
-      const unsigned long long kr = tv.r[k], ki = tv.i[k];
-      fp.re[k] = fma2(CR, kr, fp.re[k]);
-      fp.re[k] = fma2(BE, ki, fp.re[k]);
-      fp.im[k] = fma2(CI, kr, fp.im[k]);
-      fp.im[k] = fma2(DE, ki, fp.im[k]);
+      for (int r = 0; r < L::R; ++r) {
+        const unsigned long long t = tap_pair<T, kGlobal>(p + r * L::BB);
+        fp.p1[r] = fma2(op.x, t, fp.p1[r]);
+        fp.p2[r] = fma2(op.y, t, fp.p2[r]);
+      }
     }
-    if (L::RT) {
-      fp.tre = fmaf(cr, tv.tr, fp.tre);
-      fp.tre = fmaf(be, tv.ti, fp.tre);
-      fp.tim = fmaf(cim, tv.tr, fp.tim);
-      fp.tim = fmaf(de, tv.ti, fp.tim);
+    if (!last) {
+      q += kRingRecs;
+      continue;
     }
+    if (nb >= ne) break;
+    if (nb != ce) {                                        // not the continuation of this batch
+      fp.flush(cz != kNoOrigin, grid, cidx, n, nrow);
+      fp.zero();
+      cz = kNoOrigin;
+      cj0 = -1;
+    }
+    cb = nb;
+    ce = ne;
+    q = cb;
+    grab(nb, ne);
   }
-  fp.flush(cz != kNoOrigin, grid, cidx, (uint32_t)n, nrow);
+  fp.flush(cz != kNoOrigin, grid, cidx, n, nrow);
 }
 
+// The records [pb, pe) of plane p (support S) with the whole CTA: stage the plane's table
+// unless it is staged already (or too large: then its global copy is read), and walk the
+// records: for S <= 16 each warp takes batches of kBatch from a counter, so that dense and
+// sparse regions even out; for S > 16 each pair of warps (one per row half) walks one
+// contiguous piece.
 template <int S, class T>
-__device__ __noinline__ void grid_segment(const G2Args& a, int p, bool stage, bool staged, int x0, int y0, int width,
-                                          uint32_t s0, uint32_t s1, int cap, int tab_off, int rec_off) {
+__device__ __noinline__ void grid_plane(const G2Args& a, int p, bool stage, bool staged, uint32_t pb, uint32_t pe) {
   using L = Lay<S, T>;
-  if (staged && stage) stage_table<S, T>((const T*)a.tab + a.tab_off[p], a.g.os, tab_off);
+  __shared__ uint32_t next;
+  const int tab_off = kRingsBytes;
+  __syncthreads();                                 // every warp is done with the previous plane
+  if (threadIdx.x == 0) next = pb;
+  if (stage) stage_table<S, T>((const T*)a.tab + a.tab_off[p], a.g.os, tab_off);
+  __syncthreads();
   const unsigned char* gtab = staged ? nullptr : a.lanetab + a.lanetab_off[p];
-  const int keys = width * a.g.tile_y;
   const int warp = threadIdx.x >> 5;
-  constexpr int kPieces = kWarps / L::H;            // warps of a row-half pair share a piece
-  const int piece = warp / L::H, h = warp % L::H;
-  for (uint32_t c0 = s0; c0 < s1; c0 += (uint32_t)cap) {
-    const int m = (int)min((uint32_t)cap, s1 - c0);
-    sort_chunk<S, T>((const uint4*)a.recs, nullptr, c0, m, x0, y0, width, keys, a.g.os, rec_off);
-    const int beg = (int)((int64_t)m * piece / kPieces), end = (int)((int64_t)m * (piece + 1) / kPieces);
-    if (L::H == 1 || staged) warp_grid<S, T, false>(tab_off, nullptr, h, rec_off, beg, end, a.grid, a.g.n);
-    else warp_grid<S, T, true>(tab_off, gtab, h, rec_off, beg, end, a.grid, a.g.n);
-    __syncthreads();
+  const int ring_off = warp * kRingBytes;
+  uint32_t sbeg = 0, send = 0;
+  if constexpr (L::H > 1) {
+    constexpr int kPieces = kWarps / L::H;
+    const int piece = warp / L::H;
+    const uint32_t nrec = pe - pb;
+    sbeg = pb + (uint32_t)((uint64_t)nrec * piece / kPieces);
+    send = pb + (uint32_t)((uint64_t)nrec * (piece + 1) / kPieces);
   }
+  uint32_t* ctr = L::H > 1 ? nullptr : &next;
+  const int h = warp % L::H;
+  if (staged) warp_grid<S, T, false>(a, tab_off, nullptr, h, ring_off, pe, ctr, sbeg, send);
+  else warp_grid<S, T, true>(a, tab_off, gtab, h, ring_off, pe, ctr, sbeg, send);
 }
 
-// Grids the records [beg, end) of the (plane, tile)-sorted array, segment by segment.
+// cur_plane: the plane whose table is staged (-1: none), the same in every thread of the CTA.
 template <class T>
-__device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end) {
+__device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end, int& cur_plane) {
   int64_t bin = find_bin(a.offsets, a.nbins, beg);
   uint32_t pos = beg;
-  int cur_plane = -1;
-  const int tab_off = kCountsBytes;
+  const int tab_off = kRingsBytes;
   while (pos < end) {
     bin = advance_bin(a.offsets, bin, a.nbins, pos);
     const int p = (int)(bin / a.g.ntiles);
-    const int64_t tile = bin - (int64_t)p * a.g.ntiles;
-    const int ty = (int)(tile / a.g.ntx), tx = (int)(tile - (int64_t)ty * a.g.ntx);
+    const uint32_t pe = min(end, a.offsets[(int64_t)(p + 1) * a.g.ntiles]);
     const int s = a.g.supp[p];
-    // tables of S > 16 are staged too when they leave room for a chunk of kStagedChunk records
     const int tbytes = a.g.os * a.g.os * lay_class_bytes(s, TabElem<T>::E);
-    const bool staged = s <= kMaxStagedS || tab_off + tbytes + kStagedChunk * (int)sizeof(Record) <= a.smem_bytes;
-    const int rec_off = tab_off + (staged ? tbytes : 0);
-    const int cap = min(kMaxChunk, (a.smem_bytes - rec_off) / (int)sizeof(Record));
-    int ntiles = 1;
-    const uint32_t seg_end = segment_end(a.offsets, a.nbins, bin, tx, a.g.ntx, pos, end, cap, a.group_tiles, &ntiles);
+    const bool staged = s <= kMaxStagedS || tab_off + tbytes <= a.smem_bytes;
     const bool stage = staged && p != cur_plane;
-    cur_plane = staged ? p : -1;                  // an unstaged segment's records overwrite the table
-    const int x0 = tx * a.g.tile_x, y0 = ty * a.g.tile_y;
-    const int width = ntiles * a.g.tile_x;
+    if (staged) cur_plane = p;
     switch (s) {
-#define WP_SEG_CASE(N)                                                                   \
-  case N:                                                                                \
-    grid_segment<N, T>(a, p, stage, staged, x0, y0, width, pos, seg_end, cap, tab_off, rec_off);   \
+#define WP_SEG_CASE(N)                                      \
+  case N:                                                   \
+    grid_plane<N, T>(a, p, stage, staged, pos, pe);         \
     break;
       WP_SEG_CASE(1) WP_SEG_CASE(2) WP_SEG_CASE(3) WP_SEG_CASE(4) WP_SEG_CASE(5) WP_SEG_CASE(6) WP_SEG_CASE(7)
       WP_SEG_CASE(8) WP_SEG_CASE(9) WP_SEG_CASE(10) WP_SEG_CASE(11) WP_SEG_CASE(12) WP_SEG_CASE(13)
@@ -215,24 +282,25 @@ __device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end) {
       default:
         break;
     }
-    pos = seg_end;
+    pos = pe;
   }
 }
 
 template <class T>
 __global__ void __launch_bounds__(kThreads, 1) k_grid_v2(G2Args a) {
+  int cur_plane = -1;
   for_each_unit<true>(a.offsets, a.costoff, a.nbins, a.nunits, a.work,
-                [&](uint32_t beg, uint32_t end) { grid_range<T>(a, beg, end); });
+                      [&](uint32_t beg, uint32_t end) { grid_range<T>(a, beg, end, cur_plane); });
 }
 
-// ---- lane-order tables in global memory for the planes with S > 16 ----
+// ---- tap-layout tables in global memory for the planes with S > 16 ----
 
-// Writes plane tables (stored layout [oy*os+ox][a][b] of T) in the lane order of Lay<S> with
-// two row halves, for a runtime support s (17 .. 32); grid-stride over the table's entries.
+// Writes a plane's table (stored layout [oy*os+ox][a][b] of T) in the tap layout for a runtime
+// support s (17 .. 32); grid-stride over the table's entries.
 template <class T>
 __global__ void k_lane_table(const T* __restrict__ src, int s, int os, unsigned char* __restrict__ dst) {
-  const int n = half_entries(os, s);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) write_half_entry<T>(src, s, dst, i);
+  const int n = tap_entries(os, s);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) write_tap_entry<T>(src, s, dst, i);
 }
 
 // ---- many jobs in one persistent launch (wp_batch_grid) ----
@@ -292,7 +360,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_batch(BatchArgs b) {
       const G2Args a = b.jobs[j];
       const uint64_t lo = max(x0, b.jobcost[j]) - b.jobcost[j], hi = min(x1, b.jobcost[j + 1]) - b.jobcost[j];
       const uint32_t beg = job_split(a, lo), end = job_split(a, hi);
-      if (beg < end) grid_range<T>(a, beg, end);
+      int cur_plane = -1;                          // another job's tables
+      if (beg < end) grid_range<T>(a, beg, end, cur_plane);
     }
   }
   if (threadIdx.x == 0) {
@@ -308,23 +377,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_batch(BatchArgs b) {
 }  // namespace
 
 // Dynamic shared memory of the launch (the device's opt-in maximum), or 0 when the geometry
-// is outside the kernel's limits (then the baseline kernel of grid.cu runs).
+// is outside the kernel's limits (then the baseline kernel of grid.cu runs): supports up to 32,
+// and the warps' rings plus the largest table of S <= 16 within the device's shared memory
+// (larger supports read a global copy of their table when it does not fit).
 size_t grid_v2_smem(const wp_ctx* ctx, int* group_tiles) {
   const int smax = *std::max_element(ctx->supp.begin(), ctx->supp.end());
   if (smax > kMaxS) return 0;
   const int e = ctx->prm.table_type == WP_TABLE_F32 ? 4 : 2;
   const int os = ctx->prm.oversample;
-  const int tx = ctx->geo.tile_x, ty = ctx->geo.tile_y;
-  if ((int64_t)tx * ty > kMaxKeys) return 0;
   int optin = 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->prm.device) != cudaSuccess)
     return 0;
-  const size_t bytes = (size_t)optin - 1024;        // room for the static scan scratch
+  const size_t bytes = (size_t)optin - 1024;        // room for the static scratch
   size_t tab = 0;
   for (int sp : ctx->supp) tab = std::max(tab, (size_t)lay_staged_bytes(os, sp, e));
   if (smax > kMaxStagedS && !ctx->d_lanetab) return 0;
-  if ((size_t)kCountsBytes + tab + (size_t)kMinChunk * sizeof(Record) > bytes) return 0;
-  *group_tiles = std::max(1, std::min(8, kMaxKeys / (tx * ty)));
+  if ((size_t)kRingsBytes + tab > bytes) return 0;
+  *group_tiles = 1;
   return bytes;
 }
 
@@ -358,7 +427,7 @@ cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used
   };
   switch (ctx->prm.table_type) {
     case WP_TABLE_F16: return run(k_grid_v2<__half2>);
-    case WP_TABLE_BF16: return run(k_grid_v2<__nv_bfloat162>);
+    case WP_TABLE_BF16: return run(k_grid_v2<BfWord>);
     default: return run(k_grid_v2<float2>);
   }
 }
@@ -395,7 +464,7 @@ void grid_job_desc(wp_ctx* ctx, float2* grid, size_t smem, void* out) {
 cudaError_t prepare_grid_batch(int table_type, size_t smem) {
   switch (table_type) {
     case WP_TABLE_F16: return cudaFuncSetAttribute(k_grid_batch<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    case WP_TABLE_BF16: return cudaFuncSetAttribute(k_grid_batch<__nv_bfloat162>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    case WP_TABLE_BF16: return cudaFuncSetAttribute(k_grid_batch<BfWord>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     default: return cudaFuncSetAttribute(k_grid_batch<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
 }
@@ -413,7 +482,7 @@ cudaError_t launch_grid_batch(const void* d_jobs, int njobs, uint64_t* d_jobcost
   b.work = d_work;
   switch (table_type) {
     case WP_TABLE_F16: k_grid_batch<__half2><<<nsm, kThreads, smem, s>>>(b); break;
-    case WP_TABLE_BF16: k_grid_batch<__nv_bfloat162><<<nsm, kThreads, smem, s>>>(b); break;
+    case WP_TABLE_BF16: k_grid_batch<BfWord><<<nsm, kThreads, smem, s>>>(b); break;
     default: k_grid_batch<float2><<<nsm, kThreads, smem, s>>>(b); break;
   }
   return cudaGetLastError();
@@ -436,13 +505,13 @@ cudaError_t launch_lane_tables(wp_ctx* ctx, cudaStream_t s) {
     if (ctx->lanetab_off[p] < 0) continue;
     const int sp = ctx->supp[p];
     unsigned char* dst = (unsigned char*)ctx->d_lanetab + ctx->lanetab_off[p];
-    const int blocks = std::min(1024, (os * os * 2 * 32 * 16 + 255) / 256);
+    const int blocks = std::min(1024, (tap_entries(os, sp) + 255) / 256);
     switch (ctx->prm.table_type) {
       case WP_TABLE_F16:
         k_lane_table<__half2><<<blocks, 256, 0, s>>>((const __half2*)ctx->d_tab + ctx->tab_off[p], sp, os, dst);
         break;
       case WP_TABLE_BF16:
-        k_lane_table<__nv_bfloat162><<<blocks, 256, 0, s>>>((const __nv_bfloat162*)ctx->d_tab + ctx->tab_off[p], sp,
+        k_lane_table<BfWord><<<blocks, 256, 0, s>>>((const BfWord*)ctx->d_tab + ctx->tab_off[p], sp,
                                                             os, dst);
         break;
       default:

@@ -15,6 +15,7 @@ namespace wp {
 
 constexpr double kCLight = 299792458.0;
 constexpr double kCoordLimit = 1073741824.0;  // 2^30: |U|, |V| bound for the int32 path
+constexpr int kBinSortMaxKeys = 4096;          // origins of one tile the plan's origin sort handles
 
 // Imaging geometry used by the coordinate and binning kernels (passed by value).
 struct Geometry {
@@ -26,6 +27,16 @@ struct Geometry {
   double os_l;          // os * (N * cell)
   double wscale;        // (Nw - 1) / w_max, 0 if Nw == 1
   const int32_t* supp;  // [Nw] device
+};
+
+// Stored element of a WP_TABLE_BF16 kernel table: one 32-bit word per complex tap, read as
+//   kr = the word shifted left by 16, as float32 (exactly kr rounded to bfloat16), and
+//   ki = the whole word as float32 (its high 16 bits chosen so that, with kr's 16 bits below
+//        them, the float32 value is the nearest such value to ki: within half a bfloat16 ulp).
+// Both components thus carry bfloat16 precision, and a kernel widens a tap to the float32 pair
+// (kr, ki) with one shift instead of two conversions.
+struct __align__(4) BfWord {
+  uint32_t w;
 };
 
 // One gridded (or degridded) visibility after binning: 16 bytes.
@@ -112,10 +123,14 @@ struct wp_ctx {
   double* d_chan = nullptr;            // [max_chan][2]: kx_c, kw_c
   int32_t max_chan = 0;
   wp::DeviceBuffer records;
+  wp::DeviceBuffer records2;           // the origin sort's output; swapped with records after it
   wp::DeviceBuffer rounded;            // [3][nvis] int32 rounded coordinates (plan scratch)
   wp::DeviceBuffer coord_scratch;      // wp_grid_baseline: [ngridded][8] int32 coordinates
   wp::DeviceBuffer bl_scratch;         // wp_baseline_order: row baseline indices, counts, cursors
   wp::DeviceBuffer rec_index;          // [records] uint32: visibility index | partner << 31 (wp_grid)
+  wp::DeviceBuffer rec_index2;         // the origin sort's output for rec_index
+  uint32_t* d_binlist = nullptr;       // [nbins] the non-empty bins (origin sort work list)
+  uint32_t* d_binwork = nullptr;       // [4]: list lengths (large, other bins), next entry, finished CTAs
   bool have_grid_plan = false;         // records/rec_index hold the last wp_grid's binning
   int64_t plan_nrow = 0;
   int32_t plan_nchan = 0;

@@ -16,10 +16,11 @@ namespace {
 constexpr int64_t kMaxRecords = int64_t(1) << 20;  // gridded visibilities per call (pairs count twice)
 constexpr int32_t kMaxChannels = 4096;
 constexpr size_t kRecordBytes = sizeof(wp::Record) * (size_t)kMaxRecords;
-constexpr size_t kScratchBytes = kRecordBytes + sizeof(double) * 2 * (size_t)kMaxChannels;
+// the binned records, the same records sorted by footprint origin, the channel factors
+constexpr size_t kScratchBytes = 2 * kRecordBytes + sizeof(double) * 2 * (size_t)kMaxChannels;
 constexpr int kMaxDevices = 64;
 
-// 16 MiB + 64 KiB on every GPU that loads this library, held until the process exits.
+// 32 MiB + 64 KiB on every GPU that loads this library, held until the process exits.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mutex;
@@ -67,17 +68,21 @@ int reject(wp_ctx* ctx, int code, const std::string& msg) {
 // Points the context's per-call scratch at g_scratch for the duration of one call.
 struct ScratchView {
   wp_ctx* ctx;
-  wp::DeviceBuffer records;
+  wp::DeviceBuffer records, records2;
   double* chan;
   int32_t max_chan;
-  ScratchView(wp_ctx* c, void* base) : ctx(c), records(c->records), chan(c->d_chan), max_chan(c->max_chan) {
+  ScratchView(wp_ctx* c, void* base)
+      : ctx(c), records(c->records), records2(c->records2), chan(c->d_chan), max_chan(c->max_chan) {
     ctx->records.ptr = base;
     ctx->records.bytes = kRecordBytes;
-    ctx->d_chan = (double*)((unsigned char*)base + kRecordBytes);
+    ctx->records2.ptr = (unsigned char*)base + kRecordBytes;
+    ctx->records2.bytes = kRecordBytes;
+    ctx->d_chan = (double*)((unsigned char*)base + 2 * kRecordBytes);
     ctx->max_chan = kMaxChannels;
   }
   ~ScratchView() {
     ctx->records = records;
+    ctx->records2 = records2;
     ctx->d_chan = chan;
     ctx->max_chan = max_chan;
   }

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "internal.h"
 
@@ -371,6 +372,140 @@ __global__ void k_gather_offsets(const uint32_t* __restrict__ suboff, int64_t nb
   if (b <= nbins) offsets[b] = suboff[b << nsub_log2];
 }
 
+// ---- pass 4: the records of every bin sorted by footprint origin ----
+
+// The non-empty bins as a work list: bins of at least kBigBin records from the front
+// (list[0 .. count[0])), the others from the back (list[nbins - count[1] .. nbins)), so that the
+// largest bins are taken first. count[0..1] start at zero.
+constexpr uint32_t kBigBin = 8192;
+
+__global__ void k_list_bins(const uint32_t* __restrict__ offsets, int64_t nbins, uint32_t* __restrict__ list,
+                            uint32_t* __restrict__ count) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  const uint32_t n = offsets[b + 1] - offsets[b];
+  if (n >= kBigBin) list[atomicAdd(&count[0], 1u)] = (uint32_t)b;
+  else if (n > 0) list[nbins - 1 - atomicAdd(&count[1], 1u)] = (uint32_t)b;
+}
+
+// Work item i of the bin list (i < count[0] + count[1]).
+__device__ __forceinline__ uint32_t listed_bin(const uint32_t* __restrict__ list, const uint32_t* count, int64_t nbins,
+                                               uint32_t i) {
+  return i < count[0] ? list[i] : list[nbins - 1 - (i - count[0])];
+}
+
+constexpr int kBinSortBatch = 4;     // records per thread with their loads in flight together
+
+constexpr int kBinSortThreads = 1024;
+
+// One CTA per non-empty bin (taken from a counter): a counting sort of the bin's records by the
+// origin key (j0 - y0) tile_x + (i0 - x0) of its tile (row-major), from `in` to the same positions
+// of `out`, and of the visibility indices along with them when given. Shared memory: the key
+// counts (then run starts) and cursors, 2 (tile_x tile_y + 1) words. work[0] is the bin counter
+// and work[1] counts finished CTAs; the last CTA resets both.
+__global__ void __launch_bounds__(kBinSortThreads) k_bin_sort(const uint4* __restrict__ in,
+                                                              const uint32_t* __restrict__ in_idx,
+                                                              uint4* __restrict__ out, uint32_t* __restrict__ out_idx,
+                                                              const uint32_t* __restrict__ offsets, int64_t nbins,
+                                                              const uint32_t* __restrict__ list,
+                                                              const uint32_t* __restrict__ nlist, Geometry g,
+                                                              uint32_t* __restrict__ work) {
+  extern __shared__ uint32_t sort_smem[];
+  __shared__ uint32_t item;
+  __shared__ uint32_t warp_sums[kBinSortThreads / 32];
+  const int keys = g.tile_x * g.tile_y;
+  uint32_t* cnt = sort_smem;               // [keys + 1]
+  uint32_t* cur = sort_smem + keys + 1;    // [keys + 1]
+  const uint32_t total = nlist[0] + nlist[1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (;;) {
+    if (tid == 0) item = atomicAdd(&work[0], 1u);
+    __syncthreads();
+    const uint32_t it = item;
+    __syncthreads();
+    if (it >= total) break;
+    const uint32_t b = listed_bin(list, nlist, nbins, it);
+    const uint32_t s0 = offsets[b], s1 = offsets[b + 1];
+    const int64_t tile = (int64_t)b % g.ntiles;
+    const int y0 = (int)(tile / g.ntx) * g.tile_y, x0 = (int)(tile % g.ntx) * g.tile_x;
+    for (int k = tid; k <= keys; k += kBinSortThreads) cnt[k] = 0u;
+    __syncthreads();
+    for (uint32_t r0 = s0 + tid; r0 < s1; r0 += kBinSortBatch * kBinSortThreads) {
+      uint32_t z[kBinSortBatch];
+#pragma unroll
+      for (int u = 0; u < kBinSortBatch; ++u) {
+        const uint32_t r = r0 + u * kBinSortThreads;
+        z[u] = r < s1 ? __ldg(&in[r].z) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < kBinSortBatch; ++u)
+        if (r0 + u * kBinSortThreads < s1)
+          atomicAdd(&cnt[((int)(z[u] >> 16) - y0) * g.tile_x + ((int)(z[u] & 0xffff) - x0)], 1u);
+    }
+    __syncthreads();
+    // exclusive scan of cnt[0 .. keys] (keys + 1 <= 4097 entries, up to 5 per thread)
+    const int per = (keys + 1 + kBinSortThreads - 1) / kBinSortThreads;
+    const int beg = tid * per;
+    uint32_t local = 0;
+    for (int i = 0; i < per; ++i)
+      if (beg + i <= keys) local += cnt[beg + i];
+    uint32_t x = local;
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t v = warp_sums[lane];
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += y;
+      }
+      warp_sums[lane] = v;
+    }
+    __syncthreads();
+    uint32_t run = (warp ? warp_sums[warp - 1] : 0u) + x - local;
+    for (int i = 0; i < per; ++i) {
+      if (beg + i <= keys) {
+        const uint32_t v = cnt[beg + i];
+        cur[beg + i] = run;
+        run += v;
+      }
+    }
+    __syncthreads();
+    for (uint32_t r0 = s0 + tid; r0 < s1; r0 += kBinSortBatch * kBinSortThreads) {
+      uint4 rec[kBinSortBatch];
+      uint32_t idx[kBinSortBatch];
+#pragma unroll
+      for (int u = 0; u < kBinSortBatch; ++u) {
+        const uint32_t r = r0 + u * kBinSortThreads;
+        const uint32_t rr = min(r, s1 - 1);
+        rec[u] = __ldcs(&in[rr]);
+        idx[u] = in_idx ? in_idx[rr] : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < kBinSortBatch; ++u) {
+        if (r0 + u * kBinSortThreads < s1) {
+          const int key = ((int)(rec[u].z >> 16) - y0) * g.tile_x + ((int)(rec[u].z & 0xffff) - x0);
+          const uint32_t pos = s0 + atomicAdd(&cur[key], 1u);
+          out[pos] = rec[u];
+          if (in_idx) out_idx[pos] = idx[u];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&work[1], 1u) == gridDim.x - 1) {
+      work[0] = 0u;
+      work[1] = 0u;
+      __threadfence();
+    }
+  }
+}
+
 int grid_blocks(int64_t work, int nsm) {
   const int64_t want = (work + 255) / 256;
   const int64_t cap = (int64_t)nsm * 16;
@@ -424,6 +559,26 @@ cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const
                                      ctx->geo, ctx->d_cursor, (Record*)ctx->records.ptr, rounded, index,
                                      ctx->nsub_log2);
     if ((e = cudaGetLastError())) return e;
+  }
+  // pass 4: every bin's records sorted by footprint origin, into the second record buffer, which
+  // then becomes the context's record buffer (skipped when the buffers or the origin keys of a
+  // tile do not fit: the kernels are correct for any order within a bin, only slower)
+  const int keys = ctx->geo.tile_x * ctx->geo.tile_y;
+  const bool index_ok = !index || ctx->rec_index2.bytes >= nrec * 4;
+  if (nvis > 0 && keys <= kBinSortMaxKeys && ctx->records2.bytes >= nrec * sizeof(Record) && index_ok) {
+    if ((e = cudaMemsetAsync(ctx->d_binwork, 0, 2 * sizeof(uint32_t), s))) return e;
+    k_list_bins<<<(unsigned)((ctx->nbins + 255) / 256), 256, 0, s>>>(ctx->d_offsets, ctx->nbins, ctx->d_binlist,
+                                                                      ctx->d_binwork);
+    if ((e = cudaGetLastError())) return e;
+    const size_t smem = 2 * sizeof(uint32_t) * (size_t)(keys + 1);
+    k_bin_sort<<<ctx->nsm * 2, kBinSortThreads, smem, s>>>(
+        (const uint4*)ctx->records.ptr, index, (uint4*)ctx->records2.ptr,
+        index ? (uint32_t*)ctx->rec_index2.ptr : nullptr, ctx->d_offsets, ctx->nbins, ctx->d_binlist, ctx->d_binwork,
+        ctx->geo, ctx->d_binwork + 2);
+    if ((e = cudaGetLastError())) return e;
+    ctx->launches += 2;
+    std::swap(ctx->records, ctx->records2);
+    if (index) std::swap(ctx->rec_index, ctx->rec_index2);
   }
   return cudaSuccess;
 }

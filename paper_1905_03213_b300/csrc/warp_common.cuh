@@ -27,31 +27,26 @@ constexpr int kMaxChunk = kThreads * kSortPer;                 // records of one
 constexpr uint32_t kNoOrigin = 0xffffffffu;
 constexpr int kUnitsPerCta = 6;                              // work units per CTA, on average
 
-
-// Lane layout for support S <= 16: G row groups of S lanes; lane g*S + a holds rows g*R ..
-// g*R + R - 1 of footprint column a, as RP row pairs and RT (0/1) single tail row. For
-// 16 < S <= 32 (H = 2 row halves) two warps share the records of one piece: lane a of warp
-// half h holds rows h*R .. h*R + R - 1 (R = ceil(S/2)) of column a.
-//
-// Table of one oversampling class in lane order, for tap components of E bytes (4: f32, 2:
-// f16/bf16), one entry per lane in 32-lane blocks (lanes and rows outside the footprint hold
-// zeros), per row half:
-//   f32:     per row pair k a block of float2 {kr(2k), kr(2k+1)} then a block of float2
-//            {ki(2k), ki(2k+1)}; then for the tail row a block of float2 {kr, ki}.
-//   f16/bf16: per row pair k one block of 8-byte entries {kr(2k), kr(2k+1), ki(2k), ki(2k+1)};
-//            then for the tail row a block of 4-byte entries {kr, ki}.
-// Either way a lane reads 8 bytes per row pair and load instruction. Tables of S <= 16 are
-// staged in shared memory per plane; for S > 16 a copy in this layout is built in global memory
-// once (it does not fit shared memory at oversampling 8) and read through the L1/L2 path.
+// Lane layout. For support S <= 16 the warp's lanes form G row groups of S lanes; lane
+// g*S + e holds rows g*R .. g*R + R - 1 of one footprint column. For 16 < S <= 32 (H = 2 row
+// halves) two warps share the records of one piece: lane e < S of warp half h holds rows
+// h*R .. h*R + R - 1 (R = ceil(S/2)). NL lanes hold a column; the others hold nothing.
 __host__ __device__ constexpr int lay_halves(int s) { return s > kMaxStagedS ? 2 : 1; }
 __host__ __device__ constexpr int lay_rows(int s) { return s > kMaxStagedS ? (s + 1) / 2 : (s + 32 / s - 1) / (32 / s); }
 __host__ __device__ constexpr int lay_groups(int s) { return s > kMaxStagedS ? 1 : (s + lay_rows(s) - 1) / lay_rows(s); }
 // rows spanned by the lanes of all groups or halves (>= s)
 __host__ __device__ constexpr int lay_span(int s) { return lay_rows(s) * (lay_groups(s) > lay_halves(s) ? lay_groups(s) : lay_halves(s)); }
-// bytes of one row half of a class, and of a class
-__host__ __device__ constexpr int lay_half_bytes(int s, int e) {
-  return ((lay_rows(s) / 2) * 128 + (lay_rows(s) & 1) * 64) * e;
-}
+
+// Tap layout of one plane's table, per oversampling class: for each row half h and lane row
+// r < R, a block of 32 slots, slot g*S + a holding tap (column a, row h*R + r or g*R + r) of
+// the class; slots of rows >= S or beyond NL are zero. A slot is 4 bytes wide: with 16-bit
+// tables it holds the stored element (__half2 or BfWord), and with float32 tables the block
+// is two 128-byte halves, the real parts of the 32 slots and then their imaginary parts. A
+// lane reads its current column's slot of each block with 4-byte loads, so any permutation of
+// the slots (the gridding kernel rotates each group's columns as the footprint slides) keeps
+// the 32 reads of one load on 32 distinct banks.
+__host__ __device__ constexpr int tap_entry_bytes(int e) { return e == 4 ? 8 : 4; }
+__host__ __device__ constexpr int lay_half_bytes(int s, int e) { return lay_rows(s) * 32 * tap_entry_bytes(e); }
 __host__ __device__ constexpr int lay_class_bytes(int s, int e) { return lay_halves(s) * lay_half_bytes(s, e); }
 // bytes of one plane's table that must fit shared memory (S <= 16; larger tables are staged
 // only when they fit beside a chunk, else read from their global copy)
@@ -70,16 +65,16 @@ struct TabElem<__half2> {
   static constexpr int E = 2;
 };
 template <>
-struct TabElem<__nv_bfloat162> {
+struct TabElem<BfWord> {
   static constexpr int E = 2;
 };
 
 template <int S, class T = float2>
 struct Lay {
   static constexpr int R = lay_rows(S), G = lay_groups(S), H = lay_halves(S), NL = G * S;
-  static constexpr int RP = R / 2, RT = R & 1, RPA = RP > 0 ? RP : 1;
   static constexpr int E = TabElem<T>::E;
-  static constexpr int PB = 128 * E;           // bytes of one row pair's blocks
+  static constexpr int SB = 4;                   // bytes between slots (float32: per component half)
+  static constexpr int BB = 32 * tap_entry_bytes(E);   // bytes of one row block
   static constexpr int HB = lay_half_bytes(S, E);
   static constexpr int CB = lay_class_bytes(S, E);
 };
@@ -155,7 +150,7 @@ __device__ __forceinline__ void block_exclusive_scan(int n) {
   __syncthreads();
 }
 
-// Packed pair of floats (two footprint rows) as one 64-bit register for fma.rn.f32x2.
+// Packed pair of floats as one 64-bit register for fma.rn.f32x2.
 __device__ __forceinline__ unsigned long long pack2(float a, float b) {
   return (unsigned long long)__float_as_uint(a) | ((unsigned long long)__float_as_uint(b) << 32);
 }
@@ -165,6 +160,11 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
                                                    unsigned long long c) {
   unsigned long long d;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
 // Vector reduction (no return value) of two floats into global memory: *p += (x, y).
@@ -179,165 +179,92 @@ __device__ __forceinline__ void red_add2_if(bool pred, float2* p, float x, float
       ::"l"(p), "f"(x), "f"(y), "r"((uint32_t)pred) : "memory");
 }
 
-__device__ __forceinline__ unsigned long long shfl_down2(unsigned long long v, int d) {
-  const uint32_t lo = __shfl_down_sync(0xffffffffu, (uint32_t)v, d);
-  const uint32_t hi = __shfl_down_sync(0xffffffffu, (uint32_t)(v >> 32), d);
-  return (unsigned long long)lo | ((unsigned long long)hi << 32);
+// One tap of the tap layout as the float32 pair (kr, ki) in a 64-bit register, from its slot
+// at p: in shared memory, or (kGlobal) in the global copy, read through the read-only path.
+template <class T, bool kGlobal>
+__device__ __forceinline__ unsigned long long tap_pair(const unsigned char* p);
+template <>
+__device__ __forceinline__ unsigned long long tap_pair<float2, false>(const unsigned char* p) {
+  return (unsigned long long)*(const uint32_t*)p | ((unsigned long long)*(const uint32_t*)(p + 128) << 32);
+}
+template <>
+__device__ __forceinline__ unsigned long long tap_pair<float2, true>(const unsigned char* p) {
+  return (unsigned long long)__ldg((const uint32_t*)p) | ((unsigned long long)__ldg((const uint32_t*)(p + 128)) << 32);
+}
+template <bool kGlobal>
+__device__ __forceinline__ unsigned long long half_pair(const unsigned char* p) {
+  const __half2 h = kGlobal ? __ldg((const __half2*)p) : *(const __half2*)p;
+  const float2 f = __half22float2(h);
+  return pack2(f.x, f.y);
+}
+template <>
+__device__ __forceinline__ unsigned long long tap_pair<__half2, false>(const unsigned char* p) {
+  return half_pair<false>(p);
+}
+template <>
+__device__ __forceinline__ unsigned long long tap_pair<__half2, true>(const unsigned char* p) {
+  return half_pair<true>(p);
+}
+// BfWord: kr = word << 16, ki = word (see BfWord)
+template <>
+__device__ __forceinline__ unsigned long long tap_pair<BfWord, false>(const unsigned char* p) {
+  const uint32_t w = *(const uint32_t*)p;
+  return (unsigned long long)(w << 16) | ((unsigned long long)w << 32);
+}
+template <>
+__device__ __forceinline__ unsigned long long tap_pair<BfWord, true>(const unsigned char* p) {
+  const uint32_t w = __ldg((const uint32_t*)p);
+  return (unsigned long long)(w << 16) | ((unsigned long long)w << 32);
 }
 
-__device__ __forceinline__ float2 to_float2(__half2 h) { return __half22float2(h); }
-__device__ __forceinline__ float2 to_float2(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+// Entry i of one plane's tap-layout table (classes x halves x R blocks x 32 slots, in that
+// order), copied from the stored layout src[(cls * S + a) * S + b] of T; written at dst.
 template <class T>
-__device__ __forceinline__ T bits_as(uint32_t u) {
-  T t;
-  memcpy(&t, &u, 4);
-  return t;
-}
-
-// This lane's taps of one record as float32: RP row pairs packed {kr(2k), kr(2k+1)} and
-// {ki(2k), ki(2k+1)} for f32x2 FMAs, and the tail row.
-template <int S, class T = float2, bool kGlobal = false>
-struct Taps {
-  unsigned long long r[Lay<S, T>::RPA], i[Lay<S, T>::RPA];
-  float tr, ti;
-  // Lanes beyond the layout (lane >= NL) read their all-zero table entries. cls_base points into
-  // shared memory, or (kGlobal) into the global lane-order copy, read through the read-only path.
-  template <class U>
-  static __device__ __forceinline__ U rd(const unsigned char* p) {
-    if constexpr (kGlobal) return __ldg((const U*)p);
-    else return *(const U*)p;
-  }
-  __device__ __forceinline__ void load(const unsigned char* cls_base, int lane) {
-    using L = Lay<S, T>;
-    if constexpr (L::E == 4) {
-#pragma unroll
-      for (int k = 0; k < L::RP; ++k) {
-        r[k] = rd<unsigned long long>(cls_base + k * L::PB + lane * 8);
-        i[k] = rd<unsigned long long>(cls_base + k * L::PB + 256 + lane * 8);
-      }
-      if (L::RT) {
-        const float2 t = rd<float2>(cls_base + L::RP * L::PB + lane * 8);
-        tr = t.x;
-        ti = t.y;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < L::RP; ++k) {
-        const uint2 v = rd<uint2>(cls_base + k * L::PB + lane * 8);
-        const float2 a = to_float2(bits_as<T>(v.x)), b = to_float2(bits_as<T>(v.y));
-        r[k] = pack2(a.x, a.y);
-        i[k] = pack2(b.x, b.y);
-      }
-      if (L::RT) {
-        const float2 t = to_float2(bits_as<T>(rd<uint32_t>(cls_base + L::RP * L::PB + lane * 4)));
-        tr = t.x;
-        ti = t.y;
-      }
-    }
-  }
-};
-
-__device__ __forceinline__ float2 tap_float2(float2 v) { return v; }
-__device__ __forceinline__ float2 tap_float2(__half2 v) { return __half22float2(v); }
-__device__ __forceinline__ float2 tap_float2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
-__device__ __forceinline__ uint32_t pack_pair(__half2, float a, float b) {
-  const __half2 h = __floats2half2_rn(a, b);
-  uint32_t u;
-  memcpy(&u, &h, 4);
-  return u;
-}
-__device__ __forceinline__ uint32_t pack_pair(__nv_bfloat162, float a, float b) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  uint32_t u;
-  memcpy(&u, &h, 4);
-  return u;
-}
-
-// Entry i of the two-row-half lane layout (16 < s <= 32) of one plane's table: the table's
-// classes x halves x (row pairs + tail) x 32 lanes entries in order; writes it below dst.
-template <class T>
-__device__ __forceinline__ void write_half_entry(const T* __restrict__ src, int s, unsigned char* dst, int i) {
-  constexpr int E = TabElem<T>::E, PB = 128 * E;
-  const int r = (s + 1) / 2, rp = r / 2, per = rp + (r & 1);
-  const int hb = lay_half_bytes(s, E), cb = 2 * hb;
-  const int cls = i / (2 * 32 * per), rem = i - cls * (2 * 32 * per);
-  const int h = rem / (32 * per), rem2 = rem - h * (32 * per);
-  const int k = rem2 >> 5, lane = rem2 & 31;
-  const bool active = lane < s;
-  const int b0 = h * r + 2 * k;
-  const T* col = src + ((int64_t)cls * s + lane) * s;
-  const float2 v0 = (active && b0 < s) ? tap_float2(col[b0]) : make_float2(0.f, 0.f);
-  unsigned char* base = dst + (int64_t)cls * cb + h * hb + k * PB;
-  if (k < rp) {
-    const float2 v1 = (active && b0 + 1 < s) ? tap_float2(col[b0 + 1]) : make_float2(0.f, 0.f);
-    if constexpr (E == 4) {
-      *(float2*)(base + lane * 8) = make_float2(v0.x, v1.x);
-      *(float2*)(base + 256 + lane * 8) = make_float2(v0.y, v1.y);
-    } else {
-      *(uint2*)(base + lane * 8) = make_uint2(pack_pair(T{}, v0.x, v1.x), pack_pair(T{}, v0.y, v1.y));
-    }
+__device__ __forceinline__ void write_tap_entry(const T* __restrict__ src, int s, unsigned char* dst, int i) {
+  const int r_rows = lay_rows(s), g_rows = lay_groups(s), halves = lay_halves(s);
+  const int per_class = halves * r_rows * 32;
+  const int cls = i / per_class, rem = i - cls * per_class;
+  const int h = rem / (r_rows * 32), rem2 = rem - h * (r_rows * 32);
+  const int r = rem2 >> 5, slot = rem2 & 31;
+  const int g = slot / s, a = slot - g * s;
+  const int b = (halves > 1 ? h : g) * r_rows + r;
+  const bool valid = slot < g_rows * s && b < s;
+  T v;
+  if (valid) v = src[((int64_t)cls * s + a) * s + b];
+  else memset(&v, 0, sizeof(T));
+  if constexpr (sizeof(T) == 8) {               // float32: real parts, then imaginary parts
+    unsigned char* blk = dst + (int64_t)(i >> 5) * 256;
+    uint32_t c[2];
+    memcpy(c, &v, 8);
+    *(uint32_t*)(blk + slot * 4) = c[0];
+    *(uint32_t*)(blk + 128 + slot * 4) = c[1];
   } else {
-    if constexpr (E == 4) *(float2*)(base + lane * 8) = v0;
-    else *(uint32_t*)(base + lane * 4) = pack_pair(T{}, v0.x, v0.y);
+    *(T*)(dst + (int64_t)i * sizeof(T)) = v;
   }
 }
-__host__ __device__ constexpr int half_entries(int os, int s) {
-  return os * os * 2 * 32 * ((s + 1) / 2 / 2 + ((s + 1) / 2 & 1));
-}
+__host__ __device__ constexpr int tap_entries(int os, int s) { return os * os * lay_halves(s) * lay_rows(s) * 32; }
 
-// Stages one plane's table (src: stored layout [oy*os+ox][a][b] of T) in the lane layout of
-// Lay<S, T> at byte offset tab_off of the dynamic shared memory. 16-bit components are copied
-// exactly (each is representable after the round trip through float32).
+// Stages one plane's table (stored layout) in the tap layout at byte offset tab_off of the
+// dynamic shared memory: a plain copy of each element into its slot.
 template <int S, class T = float2>
 __device__ __forceinline__ void stage_table(const T* __restrict__ src, int os, int tab_off) {
-  using L = Lay<S, T>;
-  if constexpr (L::H > 1) {
-    for (int i = threadIdx.x; i < half_entries(os, S); i += kThreads) write_half_entry<T>(src, S, dyn_smem() + tab_off, i);
-    return;
-  }
-  constexpr int kPer = L::RP + L::RT;           // entries per lane and class
-  const int ncls = os * os;
   unsigned char* dst = dyn_smem() + tab_off;
-  for (int i = threadIdx.x; i < ncls * 32 * kPer; i += kThreads) {
-    const int cls = i / (32 * kPer), rem = i - cls * (32 * kPer);
-    const int k = rem >> 5, lane = rem & 31;
-    const int g = lane / S, col = lane - g * S;
-    const bool active = lane < L::NL;
-    const int b0 = g * L::R + 2 * k;
-    const T* s = src + ((int64_t)cls * S + col) * S;
-    const float2 v0 = (active && b0 < S) ? tap_float2(s[b0]) : make_float2(0.f, 0.f);
-    unsigned char* base = dst + cls * L::CB + k * L::PB;
-    if (k < L::RP) {
-      const float2 v1 = (active && b0 + 1 < S) ? tap_float2(s[b0 + 1]) : make_float2(0.f, 0.f);
-      if constexpr (L::E == 4) {
-        *(float2*)(base + lane * 8) = make_float2(v0.x, v1.x);
-        *(float2*)(base + 256 + lane * 8) = make_float2(v0.y, v1.y);
-      } else {
-        *(uint2*)(base + lane * 8) = make_uint2(pack_pair(T{}, v0.x, v1.x), pack_pair(T{}, v0.y, v1.y));
-      }
-    } else {
-      if constexpr (L::E == 4) *(float2*)(base + lane * 8) = v0;
-      else *(uint32_t*)(base + lane * 4) = pack_pair(T{}, v0.x, v0.y);
-    }
-  }
+  const int n = tap_entries(os, S);
+  for (int i = threadIdx.x; i < n; i += kThreads) write_tap_entry<T>(src, S, dst, i);
 }
 
-// Counting-sorts the binned records grecs[c0, c0 + m) of one segment (origin tiles of one
+// Counting sort of the binned records grecs[c0, c0 + m) of one segment (origin tiles of one
 // tile row, columns x0 .. x0 + width, rows y0 .. y0 + tile_y) by origin key (row-major within
-// the segment) into the shared array at byte offset rec_off, decoding each into
-//   x, y : as binned;  z : i0 | j0 << 16;  w : class byte offset in the staged table | conj << 31.
+// the segment). The whole chunk is read in one round of independent loads (kSortPer per
+// thread), so the sort waits for global memory once; the counters are cleared while the
+// loads are in flight. `emit(slot, rec, idx)` writes the decoded record of slot `slot`.
 // With `index` (a gridding plan's visibility index per record, partner flag in bit 31) the
-// Hermitian partners are left out and x becomes the visibility index. Returns the number of
-// records sorted; counts[key] (the shared counters at offset 0) is then the end of each key.
-template <int S, class T = float2>
+// Hermitian partners are left out. Returns the number of records sorted; counts[key] (the
+// shared counters at offset 0) is then the end of each key.
+template <class Emit>
 __device__ __forceinline__ int sort_chunk(const uint4* __restrict__ grecs, const uint32_t* __restrict__ index,
-                                          uint32_t c0, int m, int x0, int y0, int width, int keys, int os,
-                                          int rec_off) {
-  using L = Lay<S, T>;
+                                          uint32_t c0, int m, int x0, int y0, int width, int keys, Emit emit) {
   uint32_t* counts = (uint32_t*)dyn_smem();
-  uint4* drec = (uint4*)(dyn_smem() + rec_off);
-  // the whole chunk is read in one round of independent loads (kSortPer per thread), so the
-  // sort waits for global memory once; the counters are cleared while the loads are in flight
   uint4 rec[kSortPer];
   uint32_t idx[kSortPer];
 #pragma unroll
@@ -356,14 +283,11 @@ __device__ __forceinline__ int sort_chunk(const uint4* __restrict__ grecs, const
   __syncthreads();
   block_exclusive_scan(keys + 1);
   const int kept = (int)counts[keys];
-  // decode each record into its sorted slot
 #pragma unroll
   for (int u = 0; u < kSortPer; ++u) {
     if (threadIdx.x + u * kThreads < m && !(idx[u] >> 31)) {
       const int key = ((int)(rec[u].z >> 16) - y0) * width + ((int)(rec[u].z & 0xffff) - x0);
-      const int cls = (int)((rec[u].w >> 8) & 0xff) * os + (int)(rec[u].w & 0xff);
-      const uint32_t w = (uint32_t)(cls * L::CB) | (rec[u].w & 0x80000000u);
-      drec[atomicAdd(&counts[key], 1u)] = make_uint4(index ? idx[u] : rec[u].x, rec[u].y, rec[u].z, w);
+      emit((int)atomicAdd(&counts[key], 1u), rec[u], idx[u]);
     }
   }
   __syncthreads();

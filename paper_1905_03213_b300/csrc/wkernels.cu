@@ -139,9 +139,27 @@ template <>
 __device__ __forceinline__ __half2 store_tap<__half2>(double re, double im) {
   return __halves2half2(__double2half(re), __double2half(im));
 }
+// BfWord: low 16 bits = re rounded to bfloat16; high 16 bits chosen so that the whole word, as
+// float32, is the nearest such value to im (candidates: the float32 of im truncated to its high
+// half and its two neighbours; non-finite candidates are skipped).
 template <>
-__device__ __forceinline__ __nv_bfloat162 store_tap<__nv_bfloat162>(double re, double im) {
-  return __halves2bfloat162(__double2bfloat16(re), __double2bfloat16(im));
+__device__ __forceinline__ BfWord store_tap<BfWord>(double re, double im) {
+  const __nv_bfloat16 rb = __double2bfloat16(re);
+  uint16_t lo;
+  memcpy(&lo, &rb, 2);
+  const uint32_t hi0 = __float_as_uint(__double2float_rn(im)) >> 16;
+  uint32_t best = (hi0 << 16) | lo;
+  double err = fabs((double)__uint_as_float(best) - im);
+  if (!isfinite(__uint_as_float(best))) err = INFINITY;
+  for (int dlt = -1; dlt <= 1; dlt += 2) {
+    const uint32_t w = (((hi0 + (uint32_t)dlt) & 0xffffu) << 16) | lo;
+    const float v = __uint_as_float(w);
+    if (isfinite(v) && fabs((double)v - im) < err) {
+      err = fabs((double)v - im);
+      best = w;
+    }
+  }
+  return BfWord{best};
 }
 
 // Full tables: canonical float64 [ey][ex] and the stored grid layout
@@ -216,8 +234,8 @@ cudaError_t launch_make_wkernels(wp_ctx* ctx, cudaStream_t s) {
                                                          (__half2*)ctx->d_tab, total);
       break;
     case WP_TABLE_BF16:
-      k_tables<__nv_bfloat162><<<nblk(total, 256), 256, 0, s>>>(kg, ctx->d_quad, ctx->d_nu, ctx->d_tab64_off,
-                                                                ctx->d_tab64, (__nv_bfloat162*)ctx->d_tab, total);
+      k_tables<BfWord><<<nblk(total, 256), 256, 0, s>>>(kg, ctx->d_quad, ctx->d_nu, ctx->d_tab64_off,
+                                                                ctx->d_tab64, (BfWord*)ctx->d_tab, total);
       break;
     default:
       k_tables<float2><<<nblk(total, 256), 256, 0, s>>>(kg, ctx->d_quad, ctx->d_nu, ctx->d_tab64_off, ctx->d_tab64,

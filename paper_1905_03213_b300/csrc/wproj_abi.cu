@@ -134,8 +134,10 @@ int prepare_vis_call(wp_ctx* ctx, const double* uvw, const double* freq, int64_t
   if ((rc = ensure_channels(ctx, nchan))) return rc;
   const size_t ng = (size_t)nrow * nchan * (pairs ? 2 : 1);
   if ((rc = ensure_buffer(ctx, ctx->records, std::max<size_t>(ng, 1) * sizeof(wp::Record), "records"))) return rc;
+  if ((rc = ensure_buffer(ctx, ctx->records2, std::max<size_t>(ng, 1) * sizeof(wp::Record), "sorted records"))) return rc;
   if ((rc = ensure_buffer(ctx, ctx->rounded, std::max<size_t>((size_t)nrow * nchan, 1) * 12, "coordinate scratch"))) return rc;
   if (want_index && (rc = ensure_buffer(ctx, ctx->rec_index, std::max<size_t>(ng, 1) * 4, "record indices"))) return rc;
+  if (want_index && (rc = ensure_buffer(ctx, ctx->rec_index2, std::max<size_t>(ng, 1) * 4, "sorted record indices"))) return rc;
   ctx->have_grid_plan = false;          // the records are about to be replaced
   if (nrow > 0) {
     WP_CUDA(ctx, wp::launch_channel_factors(freq, nchan, ctx->geo.os_l, ctx->geo.wscale, ctx->d_chan, s));
@@ -191,7 +193,8 @@ void wp_destroy(wp_ctx* ctx) {
                   ctx->d_wplane,   ctx->d_tab_off,   ctx->d_tab64_off, ctx->d_quad_off, ctx->d_nu,
                   ctx->d_counts,   ctx->d_offsets,   ctx->d_cursor,    ctx->d_partials, ctx->d_chan,
                   ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2, ctx->d_work, ctx->rounded.ptr, ctx->rec_index.ptr, ctx->d_suboff, ctx->d_lanetab, ctx->d_lanetab_off,
-                  ctx->coord_scratch.ptr, ctx->bl_scratch.ptr};
+                  ctx->coord_scratch.ptr, ctx->bl_scratch.ptr, ctx->records2.ptr, ctx->rec_index2.ptr,
+                  ctx->d_binlist, ctx->d_binwork};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -328,6 +331,8 @@ int wp_create(wp_ctx** out, const wp_params* p) {
             dalloc(&ctx->d_costoff, (size_t)ctx->nbins + 1) == cudaSuccess &&
             dalloc(&ctx->d_partials2, (size_t)scan_tiles + 1) == cudaSuccess &&
             dalloc(&ctx->d_work, 4) == cudaSuccess && cudaMemset(ctx->d_work, 0, 4 * sizeof(uint32_t)) == cudaSuccess &&
+            dalloc(&ctx->d_binlist, (size_t)ctx->nbins) == cudaSuccess && dalloc(&ctx->d_binwork, 4) == cudaSuccess &&
+            cudaMemset(ctx->d_binwork, 0, 4 * sizeof(uint32_t)) == cudaSuccess &&
             dalloc(&ctx->d_dropped, 1) == cudaSuccess && dalloc(&ctx->d_wsum, 1) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -611,10 +616,12 @@ int wp_wkernel_export(wp_ctx* ctx, int32_t plane, int32_t which, void* out_host,
         uint16_t hr, hi;
         std::memcpy(&hr, &raw[4 * src], 2);
         std::memcpy(&hi, &raw[4 * src + 2], 2);
-        if (ctx->prm.table_type == WP_TABLE_BF16) {
-          const uint32_t ur = (uint32_t)hr << 16, ui = (uint32_t)hi << 16;
+        if (ctx->prm.table_type == WP_TABLE_BF16) {   // BfWord: re = word << 16, im = word
+          uint32_t w;
+          std::memcpy(&w, &raw[4 * src], 4);
+          const uint32_t ur = w << 16;
           std::memcpy(&re, &ur, 4);
-          std::memcpy(&im, &ui, 4);
+          std::memcpy(&im, &w, 4);
         } else {
           re = half_to_float(hr);
           im = half_to_float(hi);
@@ -730,6 +737,7 @@ int wp_batch_create(const wp_job* jobs, int32_t njobs, wp_batch** out) {
     if ((rc = ensure_channels(ctx, j.nchan))) return rc;
     const size_t nv = (size_t)j.nrow * j.nchan, ng = nv * (pairs ? 2 : 1);
     if ((rc = ensure_buffer(ctx, ctx->records, std::max<size_t>(ng, 1) * sizeof(wp::Record), "records"))) return rc;
+    if ((rc = ensure_buffer(ctx, ctx->records2, std::max<size_t>(ng, 1) * sizeof(wp::Record), "sorted records"))) return rc;
     if ((rc = ensure_buffer(ctx, ctx->rounded, std::max<size_t>(nv, 1) * 12, "coordinate scratch"))) return rc;
     b->jobs.push_back(j);
   }

@@ -58,10 +58,9 @@ def parity_case(pairs=False, weights=True, rows=None) -> Case:
 
 
 def random_case(n=64, nrow=700, nchan=3, n_w=6, s_min=6, s_max=10, os_=8, pairs=False, seed=5,
-                off_grid=0.1) -> Case:
+                off_grid=0.1, cell=2.0 * ARCMIN) -> Case:
     """Random uvw over the grid (a fraction beyond it), several channels, w both signs."""
     rng = np.random.default_rng(seed)
-    cell = 2.0 * ARCMIN
     field = n * cell
     freqs = np.linspace(1.0e9, 1.3e9, nchan)
     lam_max = oracle.C_LIGHT / freqs.max()

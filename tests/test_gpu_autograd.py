@@ -148,3 +148,42 @@ def test_autograd_gradient_matches_oracle(torch_cuda):
     ref = oracle.fft_to_image(oracle.grid(crd, wproj.gridded_values(r, None, crd), case.tables, prm), 1.0, prm)
     e, _ = peak_rel(inner(grad.cpu().numpy()), inner(ref))
     assert e < 1e-5, e
+
+
+def test_autograd_gradient_matches_oracle_differentiable_geometry(torch_cuda):
+    """The oracle gradient at the differentiable workload's own geometry (2048^2, 32 planes,
+    support 12, oversampling 8) on a row subset: its first 60,000 rows (the first 30 time
+    samples of all 2016 baselines), a model image over the inner half."""
+    torch = torch_cuda
+    import paper_1905_03213_b300 as W
+    from paper_1905_03213_b300.autograd import predict
+    cfg = synth.config("diff")
+    enu = synth.antenna_enu(cfg.n_ant, cfg.radius_m, cfg.height_m, np.random.default_rng(cfg.seed))
+    uvw_all = synth.uvw_metres(enu, synth.SITE_LAT, cfg.dec, synth.hour_angles(cfg.n_time, cfg.duration_h))
+    w_max = float(np.abs(uvw_all[:, 2]).max() * np.max(cfg.freqs) / synth.C_LIGHT)   # planes of the full run
+    rows = 60_000
+    uvw = np.ascontiguousarray(uvw_all[:rows])
+    freqs = np.asarray(cfg.freqs, dtype=np.float64)
+    vis, _ = synth.random_visibilities(rows, len(freqs), 61)
+    prm = oracle.Params(cfg.n, cfg.cell, cfg.n_w, w_max, cfg.s_min, cfg.s_max, cfg.oversample)
+    tabs, _ = oracle.wkernels(prm)
+    wp = W.WProj(n=cfg.n, cell=cfg.cell, n_w=cfg.n_w, w_max=w_max, support_min=cfg.s_min,
+                 support_max=cfg.s_max, oversample=cfg.oversample)
+    wp.make_wkernels()
+    n = cfg.n
+    X = np.zeros((n, n), np.float32)
+    X[n // 4: 3 * n // 4, n // 4: 3 * n // 4] = np.random.default_rng(62).random((n // 2, n // 2)) * 1e-3
+    Xr = torch.from_numpy(X).cuda().requires_grad_(True)
+    d_uvw = torch.from_numpy(uvw).cuda()
+    d_f = torch.from_numpy(freqs).cuda()
+    d_vis = torch.from_numpy(vis).cuda()
+    L = torch.sum(torch.abs(predict(wp, Xr, d_uvw, d_f) - d_vis) ** 2)
+    (grad,) = torch.autograd.grad(L, Xr)
+    crd = oracle.coords(uvw, freqs, prm)
+    assert crd["keep"].sum() > 0.9 * rows
+    AX = oracle.degrid(crd, oracle.image_to_grid_adjoint(X.astype(np.float64), 1.0, prm), tabs, prm,
+                       threads=8).reshape(vis.shape)
+    r = 2.0 * (AX - vis.astype(np.complex128))
+    ref = oracle.fft_to_image(oracle.grid(crd, wproj.gridded_values(r, None, crd), tabs, prm, threads=8), 1.0, prm)
+    e, _ = peak_rel(inner(grad.cpu().numpy()), inner(ref))
+    assert e < 1e-5, e
