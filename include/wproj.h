@@ -268,7 +268,8 @@ int wp_plane_info(const wp_ctx* ctx, int32_t* support_out, double* w_out);
 
 /* The float64 coordinate step of wp_grid alone. For each gridded visibility
  * (k = r*nchan + c, then the Hermitian partners at k + nrow*nchan if flagged) writes 8
- * int32: U, V, plane, conj, keep, i0, j0, ox | (oy << 16).
+ * int32: U, V, plane, conj, keep, i0, j0, ox | (oy << 16); i0, j0, ox and oy are defined for
+ * kept visibilities only.
  *   out device [ngridded][8] int32. Errors: WP_EINVAL, WP_ECUDA. */
 int wp_coords(wp_ctx* ctx, const double* uvw, const double* freq, int64_t nrow, int32_t nchan,
               int32_t flags, int32_t* out, void* stream);

@@ -17,6 +17,32 @@ constexpr double kCLight = 299792458.0;
 constexpr double kCoordLimit = 1073741824.0;  // 2^30: |U|, |V| bound for the int32 path
 constexpr int kBinSortMaxKeys = 4096;          // origins of one tile the plan's origin sort handles
 
+// Unsigned 32-bit division by an invariant divisor d >= 1 with one multiply-high, after
+// Granlund and Montgomery, "Division by invariant integers using multiplication" (PLDI 1994,
+// Fig. 4.1): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+//   q = (t + ((n - t) >> s1)) >> s2,  t = umulhi(m, n),  s1 = min(l, 1), s2 = max(l - 1, 0),
+// which equals floor(n / d) for every 32-bit n.
+struct FastDiv {
+  uint32_t d, m;
+  int32_t s1, s2;
+  static FastDiv make(uint32_t div) {
+    FastDiv f;
+    f.d = div;
+    int l = 0;
+    while (l < 32 && (1ull << l) < div) ++l;
+    f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - div)) / div + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+  }
+#ifdef __CUDACC__
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    const uint32_t t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+#endif
+};
+
 // Imaging geometry used by the coordinate and binning kernels (passed by value).
 struct Geometry {
   int32_t n;            // N
@@ -27,6 +53,7 @@ struct Geometry {
   double os_l;          // os * (N * cell)
   double wscale;        // (Nw - 1) / w_max, 0 if Nw == 1
   const int32_t* supp;  // [Nw] device
+  FastDiv div_os, div_tx, div_ty;   // divisions by os, tile_x, tile_y
 };
 
 // Stored element of a WP_TABLE_BF16 kernel table: one 32-bit word per complex tap, read as
@@ -109,8 +136,7 @@ struct wp_ctx {
   // binning
   wp::Geometry geo{};
   int64_t nbins = 0;
-  // Each bin's counter is split into nsub sub-counters (visibility index mod nsub), so that the
-  // atomics of a dense bin spread over nsub addresses; a bin's records stay contiguous.
+  // Sub-counters per bin (2^nsub_log2; now always 1: the plan aggregates per CTA instead).
   int32_t nsub_log2 = 0;
   uint32_t* d_counts = nullptr;        // [nbins * nsub] histogram (also scratch for the work estimates)
   uint32_t* d_suboff = nullptr;        // [nbins * nsub + 1] exclusive prefix sums of the sub-counters

@@ -26,11 +26,6 @@ struct Coord {
   bool conj, keep;
 };
 
-__device__ __forceinline__ int32_t floor_div(int32_t a, int32_t b) {
-  // b > 0
-  return a >= 0 ? a / b : -((-a + b - 1) / b);
-}
-
 // Round-half-to-even of a float64 with |x| < 2^30 (the caller checks), as an integer, from
 // its bit pattern with integer operations only: x = m 2^(e - 1075) with the 53-bit
 // significand m, so the integer part is m >> (1075 - e) and the dropped bits decide the
@@ -110,16 +105,21 @@ __device__ __forceinline__ Coord make_coord(const Rounded& r, bool neg, const Ge
   const int32_t half = s * g.os / 2;
   const int32_t x = u + (g.n / 2) * g.os;
   const int32_t y = v + (g.n / 2) * g.os;
-  c.i0 = floor_div(x - half, g.os) + 1;
-  c.j0 = floor_div(y - half, g.os) + 1;
+  // floor((x - half) / os) + 1 = floor((x - half + os) / os) when x - half + os >= 0; below
+  // that the footprint starts left of cell 0 and the visibility is dropped (i0 = -1)
+  const int32_t ax = x - half + g.os, ay = y - half + g.os;
+  c.i0 = ax >= 0 ? (int32_t)g.div_os.div((uint32_t)ax) : -1;
+  c.j0 = ay >= 0 ? (int32_t)g.div_os.div((uint32_t)ay) : -1;
   c.ox = c.i0 * g.os - x + half - 1;
   c.oy = c.j0 * g.os - y + half - 1;
   c.keep = r.fin && c.i0 >= 0 && c.i0 + s <= g.n && c.j0 >= 0 && c.j0 + s <= g.n;
   return c;
 }
 
+// The (plane, origin tile) bin of a kept visibility (i0, j0 >= 0).
 __device__ __forceinline__ uint32_t bin_of(const Coord& c, const Geometry& g) {
-  return (uint32_t)((int64_t)c.plane * g.ntiles + (int64_t)(c.j0 / g.tile_y) * g.ntx + c.i0 / g.tile_x);
+  return (uint32_t)((int64_t)c.plane * g.ntiles + (int64_t)g.div_ty.div((uint32_t)c.j0) * g.ntx +
+                    g.div_tx.div((uint32_t)c.i0));
 }
 
 // Per-(row, channel) products, shared by the visibility and its Hermitian partner.
@@ -141,11 +141,6 @@ __device__ __forceinline__ Products products(const double* __restrict__ uvw, con
   return p;
 }
 
-// Sub-counter of visibility k's bin: bins are split into 2^nsub_log2 sub-counters by the low
-// bits of k, so that the atomics of one dense bin land on several addresses.
-__device__ __forceinline__ uint32_t sub_bin(uint32_t bin, int64_t k, int32_t nsub_log2) {
-  return (bin << nsub_log2) | ((uint32_t)k & ((1u << nsub_log2) - 1u));
-}
 
 __global__ void k_channel_factors(const double* __restrict__ freq, int32_t nchan, double os_l,
                                   double wscale, double* __restrict__ out) {
@@ -157,32 +152,77 @@ __global__ void k_channel_factors(const double* __restrict__ freq, int32_t nchan
   }
 }
 
+// Passes 1 and 3 give each CTA kPlanVis consecutive visibilities and count its records per bin
+// in a shared-memory hash table first, so that a bin costs one global atomic per CTA rather
+// than one per record (the records of a dense bin otherwise serialise on its counter).
+constexpr int kPlanThreads = 256;
+constexpr int kPlanPer = 4;                              // visibilities per thread
+constexpr int kPlanVis = kPlanThreads * kPlanPer;        // per CTA
+constexpr int kHashBits = 12;
+constexpr int kHashSlots = 1 << kHashBits;               // >= twice the records of a CTA (with partners)
+constexpr uint32_t kHashEmpty = 0xffffffffu;
+
+// The slot of `key` in the table (inserted if absent), or -1 if the table is full (it cannot
+// be: a CTA has at most 2 kPlanVis keys; the bound keeps the loop finite regardless).
+__device__ __forceinline__ int hash_slot(uint32_t* keys, uint32_t key) {
+  uint32_t s = (key * 2654435761u) >> (32 - kHashBits);
+  for (int i = 0; i < kHashSlots; ++i) {
+    const uint32_t prev = atomicCAS(&keys[s], kHashEmpty, key);
+    if (prev == kHashEmpty || prev == key) return (int)s;
+    s = (s + 1) & (kHashSlots - 1);
+  }
+  return -1;
+}
+
+__device__ __forceinline__ void hash_clear(uint32_t* keys, uint32_t* cnt) {
+  for (int i = threadIdx.x; i < kHashSlots; i += kPlanThreads) {
+    keys[i] = kHashEmpty;
+    cnt[i] = 0u;
+  }
+}
+
 // Pass 1: bin histogram, dropped count and kept-weight sum; optionally the rounded
 // coordinates of every visibility for pass 3.
-__global__ void __launch_bounds__(256) k_histogram(const double* __restrict__ uvw, const double* __restrict__ chan,
-                                                   const float* __restrict__ weight, int64_t nvis, int32_t nchan,
-                                                   int32_t pairs, Geometry g, uint32_t* __restrict__ counts,
-                                                   unsigned long long* __restrict__ dropped,
-                                                   double* __restrict__ wsum, int32_t* __restrict__ rounded,
-                                                   int32_t nsub_log2) {
+__global__ void __launch_bounds__(kPlanThreads) k_histogram(const double* __restrict__ uvw,
+                                                            const double* __restrict__ chan,
+                                                            const float* __restrict__ weight, int64_t nvis,
+                                                            int32_t nchan, int32_t pairs, Geometry g,
+                                                            uint32_t* __restrict__ counts,
+                                                            unsigned long long* __restrict__ dropped,
+                                                            double* __restrict__ wsum, int32_t* __restrict__ rounded) {
+  __shared__ uint32_t keys[kHashSlots], cnt[kHashSlots];
+  hash_clear(keys, cnt);
+  __syncthreads();
   double my_w = 0.0;
   unsigned long long my_drop = 0;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nvis; k += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t base = (int64_t)blockIdx.x * kPlanVis;
+#pragma unroll
+  for (int u = 0; u < kPlanPer; ++u) {
+    const int64_t k = base + u * kPlanThreads + threadIdx.x;
+    if (k >= nvis) break;
     const Products pr = products(uvw, chan, k, nchan);
     const Rounded rd = round_coords(pr.ux, pr.vy, pr.wz, pr.w, g);
     if (rounded) store_rounded(rounded, nvis, k, rd);
     int nkept = 0;
     for (int h = 0; h <= pairs; ++h) {
       const Coord c = make_coord(rd, h == 1, g);
-      if (c.keep) atomicAdd(&counts[sub_bin(bin_of(c, g), k, nsub_log2)], 1u);
+      if (c.keep) {
+        const uint32_t b = bin_of(c, g);
+        const int sl = hash_slot(keys, b);
+        if (sl >= 0) atomicAdd(&cnt[sl], 1u);
+        else atomicAdd(&counts[b], 1u);
+      }
       nkept += c.keep ? 1 : 0;
     }
     my_drop += (unsigned long long)(pairs + 1 - nkept);
     if (nkept) my_w = fma((double)(weight ? weight[k] : 1.0f), (double)nkept, my_w);
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kHashSlots; i += kPlanThreads)
+    if (keys[i] != kHashEmpty) atomicAdd(&counts[keys[i]], cnt[i]);
   // block reduction of the two scalars
-  __shared__ double sw[8];
-  __shared__ unsigned long long sd[8];
+  __shared__ double sw[kPlanThreads / 32];
+  __shared__ unsigned long long sd[kPlanThreads / 32];
   for (int off = 16; off > 0; off >>= 1) {
     my_w += __shfl_xor_sync(0xffffffffu, my_w, off);
     my_drop += __shfl_xor_sync(0xffffffffu, my_drop, off);
@@ -196,7 +236,7 @@ __global__ void __launch_bounds__(256) k_histogram(const double* __restrict__ uv
   if (threadIdx.x == 0) {
     double tw = 0.0;
     unsigned long long td = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+    for (int i = 0; i < kPlanThreads / 32; ++i) {
       tw += sw[i];
       td += sd[i];
     }
@@ -205,21 +245,50 @@ __global__ void __launch_bounds__(256) k_histogram(const double* __restrict__ uv
   }
 }
 
-// Pass 3: scatter records into their bins (coordinates from pass 1's scratch when given).
-__global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ uvw, const double* __restrict__ chan,
-                                                 const float2* __restrict__ vis, const float* __restrict__ weight,
-                                                 int64_t nvis, int32_t nchan, int32_t pairs, int32_t for_degrid,
-                                                 Geometry g, uint32_t* __restrict__ cursor,
-                                                 Record* __restrict__ records, const int32_t* __restrict__ rounded,
-                                                 uint32_t* __restrict__ index, int32_t nsub_log2) {
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nvis; k += (int64_t)gridDim.x * blockDim.x) {
-    Rounded rd;
+// Pass 3: scatter records into their bins (coordinates from pass 1's scratch when given): each
+// record's rank among the CTA's records of its bin comes from the hash table's counter, then one
+// global atomic per bin reserves the CTA's run of slots, and the records go to run start + rank.
+__global__ void __launch_bounds__(kPlanThreads) k_scatter(const double* __restrict__ uvw, const double* __restrict__ chan,
+                                                          const float2* __restrict__ vis, const float* __restrict__ weight,
+                                                          int64_t nvis, int32_t nchan, int32_t pairs, int32_t for_degrid,
+                                                          Geometry g, uint32_t* __restrict__ cursor,
+                                                          Record* __restrict__ records, const int32_t* __restrict__ rounded,
+                                                          uint32_t* __restrict__ index) {
+  __shared__ uint32_t keys[kHashSlots], cnt[kHashSlots];
+  hash_clear(keys, cnt);
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kPlanVis;
+  Rounded rd[kPlanPer];
+  uint32_t code[kPlanPer][2];                             // slot << 16 | rank, or 0xffffffff
+#pragma unroll
+  for (int u = 0; u < kPlanPer; ++u) {
+    const int64_t k = base + u * kPlanThreads + threadIdx.x;
+    code[u][0] = code[u][1] = 0xffffffffu;
+    if (k >= nvis) continue;
     if (rounded) {
-      rd = load_rounded(rounded, nvis, k);
+      rd[u] = load_rounded(rounded, nvis, k);
     } else {
       const Products pr = products(uvw, chan, k, nchan);
-      rd = round_coords(pr.ux, pr.vy, pr.wz, pr.w, g);
+      rd[u] = round_coords(pr.ux, pr.vy, pr.wz, pr.w, g);
     }
+    for (int h = 0; h <= pairs; ++h) {
+      const Coord c = make_coord(rd[u], h == 1, g);
+      if (c.keep) {
+        const uint32_t b = bin_of(c, g);
+        const int sl = hash_slot(keys, b);
+        // a full table (impossible by its size) would fall back to a per-record global cursor
+        code[u][h] = sl >= 0 ? ((uint32_t)sl << 16) | atomicAdd(&cnt[sl], 1u) : 0xfffffffeu;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kHashSlots; i += kPlanThreads)
+    if (keys[i] != kHashEmpty) cnt[i] = atomicAdd(&cursor[keys[i]], cnt[i]);
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kPlanPer; ++u) {
+    const int64_t k = base + u * kPlanThreads + threadIdx.x;
+    if (k >= nvis) continue;
     float2 val = make_float2(0.f, 0.f);
     if (!for_degrid) {
       const float2 v = vis[k];
@@ -227,22 +296,22 @@ __global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ uvw,
       val = make_float2(wt * v.x, wt * v.y);
     }
     for (int h = 0; h <= pairs; ++h) {
-      const Coord c = make_coord(rd, h == 1, g);
-      if (c.keep) {
-        const uint32_t slot = atomicAdd(&cursor[sub_bin(bin_of(c, g), k, nsub_log2)], 1u);
-        Record rec;
-        if (for_degrid) {
-          rec.x = (uint32_t)k;
-          rec.y = 0u;
-        } else {
-          rec.x = __float_as_uint(val.x);
-          rec.y = __float_as_uint(h ? -val.y : val.y);
-        }
-        rec.z = (uint32_t)c.i0 | ((uint32_t)c.j0 << 16);
-        rec.w = (uint32_t)c.ox | ((uint32_t)c.oy << 8) | (c.conj ? 0x80000000u : 0u);
-        records[slot] = rec;
-        if (index) index[slot] = (uint32_t)k | (h ? 0x80000000u : 0u);
+      if (code[u][h] == 0xffffffffu) continue;
+      const Coord c = make_coord(rd[u], h == 1, g);
+      const uint32_t slot = code[u][h] == 0xfffffffeu ? atomicAdd(&cursor[bin_of(c, g)], 1u)
+                                                      : cnt[code[u][h] >> 16] + (code[u][h] & 0xffffu);
+      Record rec;
+      if (for_degrid) {
+        rec.x = (uint32_t)k;
+        rec.y = 0u;
+      } else {
+        rec.x = __float_as_uint(val.x);
+        rec.y = __float_as_uint(h ? -val.y : val.y);
       }
+      rec.z = (uint32_t)c.i0 | ((uint32_t)c.j0 << 16);
+      rec.w = (uint32_t)c.ox | ((uint32_t)c.oy << 8) | (c.conj ? 0x80000000u : 0u);
+      records[slot] = rec;
+      if (index) index[slot] = (uint32_t)k | (h ? 0x80000000u : 0u);
     }
   }
 }
@@ -394,15 +463,57 @@ __device__ __forceinline__ uint32_t listed_bin(const uint32_t* __restrict__ list
   return i < count[0] ? list[i] : list[nbins - 1 - (i - count[0])];
 }
 
-constexpr int kBinSortBatch = 4;     // records per thread with their loads in flight together
+constexpr int kBinSortThreads = 512;
+constexpr int kBinSortPer = 8;                                   // records per thread in one chunk
+constexpr int kBinSortChunk = kBinSortThreads * kBinSortPer;     // 4096
+constexpr int kBinSortHistPer = 16;                              // keys per thread in flight (pass 1)
 
-constexpr int kBinSortThreads = 1024;
+// Exclusive scan of a[0 .. n) in place by the whole CTA (n <= 8 kBinSortThreads).
+__device__ __forceinline__ void cta_exclusive_scan(uint32_t* a, int n, uint32_t* warp_sums) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (n + kBinSortThreads - 1) / kBinSortThreads;
+  const int beg = tid * per;
+  uint32_t local = 0;
+  for (int i = 0; i < per; ++i)
+    if (beg + i < n) local += a[beg + i];
+  uint32_t x = local;
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    constexpr int kSortWarps = kBinSortThreads / 32;
+    uint32_t v = lane < kSortWarps ? warp_sums[lane] : 0u;
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, v, off);
+      if (lane >= off) v += y;
+    }
+    if (lane < kSortWarps) warp_sums[lane] = v;
+  }
+  __syncthreads();
+  uint32_t run = (warp ? warp_sums[warp - 1] : 0u) + x - local;
+  for (int i = 0; i < per; ++i) {
+    if (beg + i < n) {
+      const uint32_t v = a[beg + i];
+      a[beg + i] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+}
 
-// One CTA per non-empty bin (taken from a counter): a counting sort of the bin's records by the
-// origin key (j0 - y0) tile_x + (i0 - x0) of its tile (row-major), from `in` to the same positions
-// of `out`, and of the visibility indices along with them when given. Shared memory: the key
-// counts (then run starts) and cursors, 2 (tile_x tile_y + 1) words. work[0] is the bin counter
-// and work[1] counts finished CTAs; the last CTA resets both.
+// One CTA per non-empty bin (taken from a counter): the bin's records (and visibility indices,
+// when given) from `in` to the same range of `out`, sorted by the origin key
+// (j0 - y0) tile_x + (i0 - x0) of its tile (row-major). A chunk of up to kBinSortChunk records
+// is loaded into registers (all loads in flight together), counted per key in shared memory,
+// placed in key order in a shared-memory stage, and written out from the stage, so that the
+// global stores run along each key's records. A bin of one chunk is sorted by that alone; a
+// larger bin first counts its keys (pass 1) so that each chunk's run of a key lands after the
+// earlier chunks' runs of it. Shared memory: start[keys + 1], loc[keys + 1], the stage
+// (kBinSortChunk records and indices). work[0] is the bin counter, work[1] the finished CTAs;
+// the last CTA resets both.
 __global__ void __launch_bounds__(kBinSortThreads) k_bin_sort(const uint4* __restrict__ in,
                                                               const uint32_t* __restrict__ in_idx,
                                                               uint4* __restrict__ out, uint32_t* __restrict__ out_idx,
@@ -410,14 +521,17 @@ __global__ void __launch_bounds__(kBinSortThreads) k_bin_sort(const uint4* __res
                                                               const uint32_t* __restrict__ list,
                                                               const uint32_t* __restrict__ nlist, Geometry g,
                                                               uint32_t* __restrict__ work) {
-  extern __shared__ uint32_t sort_smem[];
+  extern __shared__ __align__(16) uint32_t sort_smem[];
   __shared__ uint32_t item;
   __shared__ uint32_t warp_sums[kBinSortThreads / 32];
   const int keys = g.tile_x * g.tile_y;
-  uint32_t* cnt = sort_smem;               // [keys + 1]
-  uint32_t* cur = sort_smem + keys + 1;    // [keys + 1]
+  const int kpad = (keys + 1 + 3) & ~3;
+  uint32_t* start = sort_smem;                          // [keys + 1]
+  uint32_t* loc = sort_smem + kpad;                     // [keys + 1]
+  uint4* stage = (uint4*)(sort_smem + 2 * kpad);        // [kBinSortChunk]
+  uint32_t* stage_idx = (uint32_t*)(stage + kBinSortChunk);
   const uint32_t total = nlist[0] + nlist[1];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   for (;;) {
     if (tid == 0) item = atomicAdd(&work[0], 1u);
     __syncthreads();
@@ -425,76 +539,72 @@ __global__ void __launch_bounds__(kBinSortThreads) k_bin_sort(const uint4* __res
     __syncthreads();
     if (it >= total) break;
     const uint32_t b = listed_bin(list, nlist, nbins, it);
-    const uint32_t s0 = offsets[b], s1 = offsets[b + 1];
+    const uint32_t s0 = offsets[b], s1 = offsets[b + 1], nrec = s1 - s0;
     const int64_t tile = (int64_t)b % g.ntiles;
     const int y0 = (int)(tile / g.ntx) * g.tile_y, x0 = (int)(tile % g.ntx) * g.tile_x;
-    for (int k = tid; k <= keys; k += kBinSortThreads) cnt[k] = 0u;
-    __syncthreads();
-    for (uint32_t r0 = s0 + tid; r0 < s1; r0 += kBinSortBatch * kBinSortThreads) {
-      uint32_t z[kBinSortBatch];
+    auto key_of = [&](uint32_t z) { return ((int)(z >> 16) - y0) * g.tile_x + ((int)(z & 0xffff) - x0); };
+    const bool multi = nrec > (uint32_t)kBinSortChunk;
+    if (multi) {                                        // pass 1: key counts of the whole bin
+      for (int k = tid; k <= keys; k += kBinSortThreads) start[k] = 0u;
+      __syncthreads();
+      for (uint32_t r0 = s0 + tid; r0 < s1; r0 += kBinSortHistPer * kBinSortThreads) {
+        uint32_t z[kBinSortHistPer];
 #pragma unroll
-      for (int u = 0; u < kBinSortBatch; ++u) {
-        const uint32_t r = r0 + u * kBinSortThreads;
-        z[u] = r < s1 ? __ldg(&in[r].z) : 0u;
-      }
+        for (int u = 0; u < kBinSortHistPer; ++u) {
+          const uint32_t r = r0 + u * kBinSortThreads;
+          z[u] = r < s1 ? __ldg(&in[r].z) : 0u;
+        }
 #pragma unroll
-      for (int u = 0; u < kBinSortBatch; ++u)
-        if (r0 + u * kBinSortThreads < s1)
-          atomicAdd(&cnt[((int)(z[u] >> 16) - y0) * g.tile_x + ((int)(z[u] & 0xffff) - x0)], 1u);
-    }
-    __syncthreads();
-    // exclusive scan of cnt[0 .. keys] (keys + 1 <= 4097 entries, up to 5 per thread)
-    const int per = (keys + 1 + kBinSortThreads - 1) / kBinSortThreads;
-    const int beg = tid * per;
-    uint32_t local = 0;
-    for (int i = 0; i < per; ++i)
-      if (beg + i <= keys) local += cnt[beg + i];
-    uint32_t x = local;
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
-      if (lane >= off) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t v = warp_sums[lane];
-      for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, v, off);
-        if (lane >= off) v += y;
+        for (int u = 0; u < kBinSortHistPer; ++u)
+          if (r0 + u * kBinSortThreads < s1) atomicAdd(&start[key_of(z[u])], 1u);
       }
-      warp_sums[lane] = v;
+      __syncthreads();
+      cta_exclusive_scan(start, keys + 1, warp_sums);
     }
-    __syncthreads();
-    uint32_t run = (warp ? warp_sums[warp - 1] : 0u) + x - local;
-    for (int i = 0; i < per; ++i) {
-      if (beg + i <= keys) {
-        const uint32_t v = cnt[beg + i];
-        cur[beg + i] = run;
-        run += v;
-      }
-    }
-    __syncthreads();
-    for (uint32_t r0 = s0 + tid; r0 < s1; r0 += kBinSortBatch * kBinSortThreads) {
-      uint4 rec[kBinSortBatch];
-      uint32_t idx[kBinSortBatch];
+    for (uint32_t c0 = s0; c0 < s1; c0 += kBinSortChunk) {
+      const int m = (int)min((uint32_t)kBinSortChunk, s1 - c0);
+      uint4 rec[kBinSortPer];
+      uint32_t idx[kBinSortPer], rank[kBinSortPer];
 #pragma unroll
-      for (int u = 0; u < kBinSortBatch; ++u) {
-        const uint32_t r = r0 + u * kBinSortThreads;
-        const uint32_t rr = min(r, s1 - 1);
-        rec[u] = __ldcs(&in[rr]);
-        idx[u] = in_idx ? in_idx[rr] : 0u;
+      for (int u = 0; u < kBinSortPer; ++u) {
+        const int i = tid + u * kBinSortThreads;
+        const uint32_t r = c0 + (uint32_t)min(i, m - 1);
+        rec[u] = __ldcs(&in[r]);
+        idx[u] = in_idx ? in_idx[r] : 0u;
+        rank[u] = 0u;
       }
+      for (int k = tid; k <= keys; k += kBinSortThreads) loc[k] = 0u;
+      __syncthreads();
 #pragma unroll
-      for (int u = 0; u < kBinSortBatch; ++u) {
-        if (r0 + u * kBinSortThreads < s1) {
-          const int key = ((int)(rec[u].z >> 16) - y0) * g.tile_x + ((int)(rec[u].z & 0xffff) - x0);
-          const uint32_t pos = s0 + atomicAdd(&cur[key], 1u);
-          out[pos] = rec[u];
-          if (in_idx) out_idx[pos] = idx[u];
+      for (int u = 0; u < kBinSortPer; ++u)
+        if (tid + u * kBinSortThreads < m) rank[u] = atomicAdd(&loc[key_of(rec[u].z)], 1u);
+      __syncthreads();
+      cta_exclusive_scan(loc, keys + 1, warp_sums);
+#pragma unroll
+      for (int u = 0; u < kBinSortPer; ++u) {
+        if (tid + u * kBinSortThreads < m) {
+          const uint32_t pos = loc[key_of(rec[u].z)] + rank[u];
+          stage[pos] = rec[u];
+          stage_idx[pos] = idx[u];
         }
       }
+      __syncthreads();
+      for (int i = tid; i < m; i += kBinSortThreads) {
+        const uint4 v = stage[i];
+        uint32_t pos = (uint32_t)i;
+        if (multi) {
+          const int k = key_of(v.z);
+          pos = start[k] + ((uint32_t)i - loc[k]);
+        }
+        out[s0 + pos] = v;
+        if (in_idx) out_idx[s0 + pos] = stage_idx[i];
+      }
+      __syncthreads();
+      if (multi) {                                      // this chunk's runs come before the next chunk's
+        for (int k = tid; k < keys; k += kBinSortThreads) start[k] += loc[k + 1] - loc[k];
+        __syncthreads();
+      }
     }
-    __syncthreads();
   }
   if (tid == 0) {
     __threadfence();
@@ -529,7 +639,7 @@ cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const
   if ((e = cudaMemsetAsync(ctx->d_counts, 0, sizeof(uint32_t) * nsub, s))) return e;
   if ((e = cudaMemsetAsync(ctx->d_dropped, 0, sizeof(unsigned long long), s))) return e;
   if ((e = cudaMemsetAsync(ctx->d_wsum, 0, sizeof(double), s))) return e;
-  const int blocks = grid_blocks(nvis, ctx->nsm);
+  const unsigned plan_blocks = (unsigned)((nvis + kPlanVis - 1) / kPlanVis);
   // pass 1 keeps the rounded coordinates for pass 3 when the context's scratch holds them
   int32_t* rounded = ctx->rounded.bytes >= (size_t)nvis * 12 ? (int32_t*)ctx->rounded.ptr : nullptr;
   // a gridding plan asked to keep its binning also records each record's visibility index, for
@@ -538,9 +648,9 @@ cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const
   uint32_t* index = (keep_index && !for_degrid && ctx->rec_index.bytes >= nrec * 4) ? (uint32_t*)ctx->rec_index.ptr : nullptr;
   ctx->launches += 4 + (nvis > 0 ? 2 : 0);  // prefix sum (3), bin offsets, histogram and scatter
   if (nvis > 0) {
-    k_histogram<<<blocks, 256, 0, s>>>(uvw, ctx->d_chan, for_degrid ? nullptr : weight, nvis, nchan, pairs ? 1 : 0,
-                                       ctx->geo, ctx->d_counts, ctx->d_dropped, ctx->d_wsum, rounded,
-                                       ctx->nsub_log2);
+    k_histogram<<<plan_blocks, kPlanThreads, 0, s>>>(uvw, ctx->d_chan, for_degrid ? nullptr : weight, nvis, nchan,
+                                                       pairs ? 1 : 0, ctx->geo, ctx->d_counts, ctx->d_dropped,
+                                                       ctx->d_wsum, rounded);
     if ((e = cudaGetLastError())) return e;
   }
   const int64_t tiles = (nsub + kScanTile - 1) / kScanTile;
@@ -555,9 +665,9 @@ cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const
                                                                           ctx->d_offsets);
   if ((e = cudaGetLastError())) return e;
   if (nvis > 0) {
-    k_scatter<<<blocks, 256, 0, s>>>(uvw, ctx->d_chan, vis, weight, nvis, nchan, pairs ? 1 : 0, for_degrid ? 1 : 0,
-                                     ctx->geo, ctx->d_cursor, (Record*)ctx->records.ptr, rounded, index,
-                                     ctx->nsub_log2);
+    k_scatter<<<plan_blocks, kPlanThreads, 0, s>>>(uvw, ctx->d_chan, vis, weight, nvis, nchan, pairs ? 1 : 0,
+                                                     for_degrid ? 1 : 0, ctx->geo, ctx->d_cursor,
+                                                     (Record*)ctx->records.ptr, rounded, index);
     if ((e = cudaGetLastError())) return e;
   }
   // pass 4: every bin's records sorted by footprint origin, into the second record buffer, which
@@ -570,7 +680,8 @@ cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const
     k_list_bins<<<(unsigned)((ctx->nbins + 255) / 256), 256, 0, s>>>(ctx->d_offsets, ctx->nbins, ctx->d_binlist,
                                                                       ctx->d_binwork);
     if ((e = cudaGetLastError())) return e;
-    const size_t smem = 2 * sizeof(uint32_t) * (size_t)(keys + 1);
+    const size_t smem = 2 * sizeof(uint32_t) * (size_t)((keys + 1 + 3) & ~3) + (size_t)kBinSortChunk * 20;
+    if ((e = cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
     k_bin_sort<<<ctx->nsm * 2, kBinSortThreads, smem, s>>>(
         (const uint4*)ctx->records.ptr, index, (uint4*)ctx->records2.ptr,
         index ? (uint32_t*)ctx->rec_index2.ptr : nullptr, ctx->d_offsets, ctx->nbins, ctx->d_binlist, ctx->d_binwork,

@@ -292,14 +292,16 @@ int wp_create(wp_ctx** out, const wp_params* p) {
   g.ntx = (q.n + g.tile_x - 1) / g.tile_x;
   g.nty = (q.n + g.tile_y - 1) / g.tile_y;
   g.ntiles = (int64_t)g.ntx * g.nty;
+  g.div_os = wp::FastDiv::make((uint32_t)g.os);
+  g.div_tx = wp::FastDiv::make((uint32_t)g.tile_x);
+  g.div_ty = wp::FastDiv::make((uint32_t)g.tile_y);
   g.os_l = (double)q.oversample * ((double)q.n * q.cell_rad);
   g.wscale = q.n_w > 1 ? (double)(q.n_w - 1) / q.w_max : 0.0;
   ctx->nbins = g.ntiles * q.n_w;
   if (ctx->nbins > (int64_t)4096 * 4096) return bail(WP_EINVAL, "too many bins (n_w * tiles > 2^24): use larger tiles");
-  // sub-counters per bin: 2, keeping nbins * nsub <= 2^24 (the prefix sum's reach). Measured on
-  // the float32 workload (32x32 tiles), planning for gridding plus degridding: 1.59 ms with 2,
-  // 1.62 with 4, 1.69 with 16, 2.37 with 1 (one counter serialises the atomics of dense bins)
-  while (ctx->nsub_log2 < 1 && (ctx->nbins << (ctx->nsub_log2 + 1)) <= (int64_t)4096 * 4096) ++ctx->nsub_log2;
+  // one counter per bin: the plan's histogram and scatter aggregate each CTA's records per bin in
+  // shared memory before their global atomics, so a dense bin's counter sees one atomic per CTA
+  ctx->nsub_log2 = 0;
   const int64_t nsubbins = ctx->nbins << ctx->nsub_log2;
   const int64_t scan_tiles = (nsubbins + 4095) / 4096;
 

@@ -89,7 +89,10 @@ def test_work_estimate_unit_rescaled():
     _grid_vs_oracle(case, tile=(tile, tile))
 
 
-@pytest.mark.parametrize("s_min,s_max,os_,table,tol", [(33, 36, 4, "f32", 1e-6), (34, 40, 2, "f16", 1e-3)])
+# the shared-memory kernel of these supports adds up to 1,296 taps per visibility into float32
+# cells with atomics, in an order that depends on the record order: the grid is held to the
+# float32 image tolerance
+@pytest.mark.parametrize("s_min,s_max,os_,table,tol", [(33, 36, 4, "f32", 1e-5), (34, 40, 2, "f16", 1e-3)])
 def test_supports_above_32(s_min, s_max, os_, table, tol):
     case = random_case(n=160, nrow=600, nchan=2, n_w=3, s_min=s_min, s_max=s_max, os_=os_, seed=47)
     _grid_vs_oracle(case, table=table, tol=tol)
