@@ -3,9 +3,10 @@
 // Degridding (Sec. 2.1 of Lao et al. 2019; the adjoint of gridding): visibility k is
 //   V_k = sum_{a,b} conj(K_k(a, b)) G(i0 + a, j0 + b),
 // with K_k = K_p for w >= 0 and conj(K_p) for w < 0. The organisation mirrors the gridding
-// kernel (grid2.cu): CTAs take work units of equal estimated work, counting-sort each chunk
-// of binned records by footprint origin in shared memory, and each warp walks a contiguous
-// piece of the sorted chunk with all 32 lanes on the same record.
+// kernel (grid2.cu): CTAs take work units of equal estimated work and decode each chunk of the
+// records, which the plan has sorted by footprint origin within every (plane, tile) bin, into
+// shared memory; each warp walks a contiguous piece of the chunk with all 32 lanes on the same
+// record.
 //
 //   * The grid region under the segment's footprints is staged in shared memory once per
 //     segment; lane (g, a) keeps the cells of its rows of footprint column a in registers
@@ -24,6 +25,8 @@
 namespace wp {
 
 namespace {
+
+constexpr int kDecodeScratch = 128;            // bytes of dynamic shared memory before the table
 
 struct D2Args {
   const Record* recs;
@@ -159,15 +162,14 @@ __device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, 
     const int gy = y0 + r, gx = x0 + c;
     sub[r * pitch + c] = (gy < a.g.n && gx < a.g.n) ? __ldg(&a.grid[(int64_t)gy * a.g.n + gx]) : make_float2(0.f, 0.f);
   }
-  const int keys = width * a.g.tile_y;
   const int warp = threadIdx.x >> 5;
   const int os = a.g.os;
   uint4* drec = (uint4*)(dyn_smem() + rec_off);
   const bool indexed = a.index != nullptr;
   for (uint32_t c0 = s0; c0 < s1; c0 += (uint32_t)cap) {
     const int m = (int)min((uint32_t)cap, s1 - c0);
-    const int kept = sort_chunk((const uint4*)a.recs, a.index, c0, m, x0, y0, width, keys,
-                                [&](int slot, const uint4& rec, uint32_t idx) {
+    const int kept = decode_chunk((const uint4*)a.recs, a.index, c0, m, (uint32_t*)dyn_smem(),
+                                  [&](int slot, const uint4& rec, uint32_t idx) {
       const int cls = (int)((rec.w >> 8) & 0xff) * os + (int)(rec.w & 0xff);
       const uint32_t sg = (rec.w & 0x80000000u) ? 0xbf800000u : 0x3f800000u;     // -1.0f or +1.0f
       drec[slot] = make_uint4(indexed ? idx : rec.x, sg, rec.z, (uint32_t)(cls * L::CB));
@@ -185,7 +187,7 @@ __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
   int64_t bin = find_bin(a.offsets, a.nbins, beg);
   uint32_t pos = beg;
   int cur_plane = -1;
-  const int tab_off = kCountsBytes;
+  const int tab_off = kDecodeScratch;          // the decode's prefix-sum scratch comes first
   while (pos < end) {
     bin = advance_bin(a.offsets, bin, a.nbins, pos);
     const int p = (int)(bin / a.g.ntiles);
@@ -251,7 +253,7 @@ size_t degrid_v2_smem(const wp_ctx* ctx, int* group_tiles) {
   for (; group >= 1; --group) {
     bool fits = true;
     for (int sp : ctx->supp) {
-      const size_t need = (size_t)kCountsBytes + (size_t)lay_staged_bytes(os, sp, e) +
+      const size_t need = (size_t)kDecodeScratch + (size_t)lay_staged_bytes(os, sp, e) +
                           (size_t)sub_bytes(tx, ty, group, sp) + (size_t)kMinChunk * sizeof(Record);
       if (need > bytes) fits = false;
     }

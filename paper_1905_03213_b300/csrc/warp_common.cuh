@@ -1,7 +1,7 @@
 // Device code shared by the warp-synchronous gridding (grid2.cu) and degridding (degrid2.cu)
 // kernels: the lane layout of a footprint over a warp, the staged kernel-table layout, the
-// in-CTA counting sort of binned records by footprint origin, the segment walk over the
-// (plane, tile) bins and the work-unit schedule. Included by exactly those two files; every
+// in-order decode of a chunk of sorted records, the segment walk over the (plane, tile) bins
+// and the work-unit schedule. Included by exactly those two files; every
 // definition has internal linkage.
 #pragma once
 
@@ -253,41 +253,53 @@ __device__ __forceinline__ void stage_table(const T* __restrict__ src, int os, i
   for (int i = threadIdx.x; i < n; i += kThreads) write_tap_entry<T>(src, S, dst, i);
 }
 
-// Counting sort of the binned records grecs[c0, c0 + m) of one segment (origin tiles of one
-// tile row, columns x0 .. x0 + width, rows y0 .. y0 + tile_y) by origin key (row-major within
-// the segment). The whole chunk is read in one round of independent loads (kSortPer per
-// thread), so the sort waits for global memory once; the counters are cleared while the
-// loads are in flight. `emit(slot, rec, idx)` writes the decoded record of slot `slot`.
-// With `index` (a gridding plan's visibility index per record, partner flag in bit 31) the
-// Hermitian partners are left out. Returns the number of records sorted; counts[key] (the
-// shared counters at offset 0) is then the end of each key.
+// Decodes the records grecs[c0, c0 + m) of one segment into the shared array the caller's
+// `emit(slot, rec, idx)` writes, in their order (the plan has sorted every bin by footprint
+// origin, and a segment's bins follow one another). Each thread takes kSortPer consecutive
+// records, all loads in flight together. With `index` (a gridding plan's visibility index per
+// record, partner flag in bit 31) the Hermitian partners are left out and the others close up.
+// Returns the number of records decoded.
+// warp_sums: kWarps words of shared memory for the prefix sum.
 template <class Emit>
-__device__ __forceinline__ int sort_chunk(const uint4* __restrict__ grecs, const uint32_t* __restrict__ index,
-                                          uint32_t c0, int m, int x0, int y0, int width, int keys, Emit emit) {
-  uint32_t* counts = (uint32_t*)dyn_smem();
+__device__ __forceinline__ int decode_chunk(const uint4* __restrict__ grecs, const uint32_t* __restrict__ index,
+                                            uint32_t c0, int m, uint32_t* warp_sums, Emit emit) {
   uint4 rec[kSortPer];
   uint32_t idx[kSortPer];
+  const int first = threadIdx.x * kSortPer;
+  int count = 0;
 #pragma unroll
   for (int u = 0; u < kSortPer; ++u) {
-    const int r = threadIdx.x + u * kThreads;
-    const int rr = min(r, m - 1);                 // m >= 1: loads past the chunk repeat its last record
-    idx[u] = index ? index[c0 + rr] : 0u;
-    rec[u] = __ldcs(grecs + c0 + rr);
+    const int i = min(first + u, m - 1);            // m >= 1: loads past the chunk repeat its last record
+    rec[u] = __ldcs(grecs + c0 + i);
+    idx[u] = index ? index[c0 + i] : 0u;
   }
-  for (int k = threadIdx.x; k <= keys; k += kThreads) counts[k] = 0u;
-  __syncthreads();
 #pragma unroll
-  for (int u = 0; u < kSortPer; ++u)
-    if (threadIdx.x + u * kThreads < m && !(idx[u] >> 31))
-      atomicAdd(&counts[((int)(rec[u].z >> 16) - y0) * width + ((int)(rec[u].z & 0xffff) - x0)], 1u);
+  for (int u = 0; u < kSortPer; ++u) count += (first + u < m && !(idx[u] >> 31)) ? 1 : 0;
+  // exclusive prefix of the threads' counts
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = (uint32_t)count;
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
   __syncthreads();
-  block_exclusive_scan(keys + 1);
-  const int kept = (int)counts[keys];
+  if (warp == 0) {
+    uint32_t v = lane < kWarps ? warp_sums[lane] : 0u;
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, v, off);
+      if (lane >= off) v += y;
+    }
+    if (lane < kWarps) warp_sums[lane] = v;
+  }
+  __syncthreads();
+  int pos = (int)((warp ? warp_sums[warp - 1] : 0u) + x) - count;
+  const int kept = (int)warp_sums[kWarps - 1];
 #pragma unroll
   for (int u = 0; u < kSortPer; ++u) {
-    if (threadIdx.x + u * kThreads < m && !(idx[u] >> 31)) {
-      const int key = ((int)(rec[u].z >> 16) - y0) * width + ((int)(rec[u].z & 0xffff) - x0);
-      emit((int)atomicAdd(&counts[key], 1u), rec[u], idx[u]);
+    if (first + u < m && !(idx[u] >> 31)) {
+      emit(pos, rec[u], idx[u]);
+      ++pos;
     }
   }
   __syncthreads();
