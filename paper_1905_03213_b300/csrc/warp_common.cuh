@@ -250,7 +250,7 @@ template <int S, class T = float2>
 __device__ __forceinline__ void stage_table(const T* __restrict__ src, int os, int tab_off) {
   unsigned char* dst = dyn_smem() + tab_off;
   const int n = tap_entries(os, S);
-  for (int i = threadIdx.x; i < n; i += kThreads) write_tap_entry<T>(src, S, dst, i);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) write_tap_entry<T>(src, S, dst, i);
 }
 
 // Decodes the records grecs[c0, c0 + m) of one segment into the shared array the caller's
