@@ -27,6 +27,12 @@ namespace wp {
 namespace {
 
 constexpr int kDecodeScratch = 128;            // bytes of dynamic shared memory before the table
+// Two launch shapes, as for gridding: 24 warps when every support is at most 16, else 16.
+constexpr int kDegridThreadsSmall = 768;
+constexpr int kDegridThreadsLarge = 512;
+constexpr int kSmallMaxS = 16;
+// records per thread in one decoded chunk; fewer with 24 warps (85 registers a thread)
+__host__ __device__ constexpr int decode_per(int threads) { return threads == kDegridThreadsSmall ? 8 : 16; }
 
 struct D2Args {
   const Record* recs;
@@ -90,12 +96,12 @@ __device__ __forceinline__ void batch_reduce(float (&v)[NB], int lane) {
 // (held as the pairs (gr, gi) and (gi, gr)):
 //   P1 += (kr, ki) * (gr, gi),  P2 += (kr, ki) * (gi, gr)
 // and its part of conj(K_k) G is (P1.x + s P1.y) + i (P2.x - s P2.y).
-template <int S, class T, bool kGlobal>
+template <int S, class T, bool kGlobal, int NT>
 __device__ __forceinline__ void warp_degrid(int tab_off, const unsigned char* gtab, int h, int sub_off, int pitch,
                                             int sx0, int sy0, int rec_off, int beg, int end,
                                             float2* __restrict__ out) {
   using L = Lay<S, T>;
-  constexpr int NB = L::R <= 5 ? 32 : (L::R <= 8 ? 16 : 8);
+  constexpr int NB = NT == kDegridThreadsSmall ? (L::R <= 8 ? 16 : 8) : (L::R <= 5 ? 32 : (L::R <= 8 ? 16 : 8));
   const int lane = threadIdx.x & 31;
   const int g = lane / S, slot = lane - g * S;
   // lanes beyond the layout read (zero-tap) cells of the half's first row
@@ -146,18 +152,18 @@ __device__ __forceinline__ void warp_degrid(int tab_off, const unsigned char* gt
   }
 }
 
-template <int S, class T>
+template <int S, class T, int NT>
 __device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, bool staged, int x0, int y0, int width,
                                             uint32_t s0, uint32_t s1, int cap, int tab_off, int sub_off,
                                             int rec_off) {
   using L = Lay<S, T>;
   if (staged && stage) stage_table<S, T>((const T*)a.tab + a.tab_off[p], a.g.os, tab_off);
   const unsigned char* gtab = staged ? nullptr : a.lanetab + a.lanetab_off[p];
-  constexpr int kPieces = kWarps / L::H;            // warps of a row-half pair share a piece
+  constexpr int kPieces = NT / 32 / L::H;          // warps of a row-half pair share a piece
   // the grid region under the segment's footprints (cells outside the grid read as zero)
   const int cols = width + S - 1, rows = sub_rows(a.g.tile_y, S), pitch = sub_pitch(cols);
   float2* sub = (float2*)(dyn_smem() + sub_off);
-  for (int i = threadIdx.x; i < rows * cols; i += kThreads) {
+  for (int i = threadIdx.x; i < rows * cols; i += NT) {
     const int r = i / cols, c = i - r * cols;
     const int gy = y0 + r, gx = x0 + c;
     sub[r * pitch + c] = (gy < a.g.n && gx < a.g.n) ? __ldg(&a.grid[(int64_t)gy * a.g.n + gx]) : make_float2(0.f, 0.f);
@@ -168,7 +174,7 @@ __device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, 
   const bool indexed = a.index != nullptr;
   for (uint32_t c0 = s0; c0 < s1; c0 += (uint32_t)cap) {
     const int m = (int)min((uint32_t)cap, s1 - c0);
-    const int kept = decode_chunk((const uint4*)a.recs, a.index, c0, m, (uint32_t*)dyn_smem(),
+    const int kept = decode_chunk<NT, decode_per(NT)>((const uint4*)a.recs, a.index, c0, m, (uint32_t*)dyn_smem(),
                                   [&](int slot, const uint4& rec, uint32_t idx) {
       const int cls = (int)((rec.w >> 8) & 0xff) * os + (int)(rec.w & 0xff);
       const uint32_t sg = (rec.w & 0x80000000u) ? 0xbf800000u : 0x3f800000u;     // -1.0f or +1.0f
@@ -176,14 +182,15 @@ __device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, 
     });
     const int piece = warp / L::H, h = warp % L::H;
     const int beg = (int)((int64_t)kept * piece / kPieces), end = (int)((int64_t)kept * (piece + 1) / kPieces);
-    if (L::H == 1 || staged) warp_degrid<S, T, false>(tab_off, nullptr, h, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
-    else warp_degrid<S, T, true>(tab_off, gtab, h, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
+    if (L::H == 1 || staged) warp_degrid<S, T, false, NT>(tab_off, nullptr, h, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
+    else warp_degrid<S, T, true, NT>(tab_off, gtab, h, sub_off, pitch, x0, y0, rec_off, beg, end, a.out);
     __syncthreads();
   }
 }
 
-template <class T>
+template <class T, int NT>
 __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
+  constexpr int kMaxSupp = NT == kDegridThreadsSmall ? kSmallMaxS : kMaxS;
   int64_t bin = find_bin(a.offsets, a.nbins, beg);
   uint32_t pos = beg;
   int cur_plane = -1;
@@ -200,7 +207,7 @@ __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
     const bool staged = s <= kMaxStagedS || tab_off + tbytes + sbytes + kStagedChunk * (int)sizeof(Record) <= a.smem_bytes;
     const int sub_off = tab_off + (staged ? tbytes : 0);
     const int rec_off = sub_off + sbytes;
-    const int cap = min(kMaxChunk, (a.smem_bytes - rec_off) / (int)sizeof(Record));
+    const int cap = min(NT * decode_per(NT), (a.smem_bytes - rec_off) / (int)sizeof(Record));
     int ntiles = 1;
     const uint32_t seg_end = segment_end(a.offsets, a.nbins, bin, tx, a.g.ntx, pos, end, cap, a.group_tiles, &ntiles);
     const bool stage = staged && p != cur_plane;
@@ -208,9 +215,10 @@ __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
     const int x0 = tx * a.g.tile_x, y0 = ty * a.g.tile_y;
     const int width = ntiles * a.g.tile_x;
     switch (s) {
-#define WP_SEG_CASE(N)                                                                                   \
-  case N:                                                                                                \
-    degrid_segment<N, T>(a, p, stage, staged, x0, y0, width, pos, seg_end, cap, tab_off, sub_off, rec_off); \
+#define WP_SEG_CASE(N)                                                                    \
+  case N:                                                                                 \
+    if constexpr (N <= kMaxSupp)                                                          \
+      degrid_segment<N, T, NT>(a, p, stage, staged, x0, y0, width, pos, seg_end, cap, tab_off, sub_off, rec_off); \
     break;
       WP_SEG_CASE(1) WP_SEG_CASE(2) WP_SEG_CASE(3) WP_SEG_CASE(4) WP_SEG_CASE(5) WP_SEG_CASE(6) WP_SEG_CASE(7)
       WP_SEG_CASE(8) WP_SEG_CASE(9) WP_SEG_CASE(10) WP_SEG_CASE(11) WP_SEG_CASE(12) WP_SEG_CASE(13)
@@ -226,10 +234,10 @@ __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(kThreads, 1) k_degrid_v2(D2Args a) {
+template <class T, int NT>
+__global__ void __launch_bounds__(NT, 1) k_degrid_v2(D2Args a) {
   for_each_unit<true>(a.offsets, a.costoff, a.nbins, a.nunits, a.work,
-                [&](uint32_t beg, uint32_t end) { degrid_range<T>(a, beg, end); });
+                      [&](uint32_t beg, uint32_t end) { degrid_range<T, NT>(a, beg, end); });
 }
 
 }  // namespace
@@ -289,16 +297,23 @@ cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* out, const
   a.work = ctx->d_work + 2;
   cudaError_t e;
   if ((e = launch_bin_costs(ctx, s))) return e;
-  auto run = [&](auto kern) -> cudaError_t {
+  const bool small = *std::max_element(ctx->supp.begin(), ctx->supp.end()) <= kSmallMaxS;
+  auto run = [&](auto kern, int threads) -> cudaError_t {
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err) return err;
-    kern<<<ctx->nsm, kThreads, smem, s>>>(a);
+    kern<<<ctx->nsm, threads, smem, s>>>(a);
     return cudaGetLastError();
   };
   switch (ctx->prm.table_type) {
-    case WP_TABLE_F16: return run(k_degrid_v2<__half2>);
-    case WP_TABLE_BF16: return run(k_degrid_v2<BfWord>);
-    default: return run(k_degrid_v2<float2>);
+    case WP_TABLE_F16:
+      return small ? run(k_degrid_v2<__half2, kDegridThreadsSmall>, kDegridThreadsSmall)
+                   : run(k_degrid_v2<__half2, kDegridThreadsLarge>, kDegridThreadsLarge);
+    case WP_TABLE_BF16:
+      return small ? run(k_degrid_v2<BfWord, kDegridThreadsSmall>, kDegridThreadsSmall)
+                   : run(k_degrid_v2<BfWord, kDegridThreadsLarge>, kDegridThreadsLarge);
+    default:
+      return small ? run(k_degrid_v2<float2, kDegridThreadsSmall>, kDegridThreadsSmall)
+                   : run(k_degrid_v2<float2, kDegridThreadsLarge>, kDegridThreadsLarge);
   }
 }
 

@@ -23,7 +23,6 @@ constexpr int kMaxKeys = 4096;                                  // origins of on
 constexpr int kCountsBytes = ((kMaxKeys + 1) * 4 + 15) & ~15;  // shared-memory counters
 constexpr int kMinChunk = 512;
 constexpr int kSortPer = 16;                                  // records per thread in one sort
-constexpr int kMaxChunk = kThreads * kSortPer;                 // records of one sorted chunk, at most
 constexpr uint32_t kNoOrigin = 0xffffffffu;
 constexpr int kUnitsPerCta = 6;                              // work units per CTA, on average
 
@@ -111,43 +110,6 @@ __device__ __forceinline__ int64_t advance_bin(const uint32_t* __restrict__ offs
     else hi = mid;
   }
   return lo;
-}
-
-// In-place exclusive scan of the shared counters counts[0..n) by the whole block.
-__device__ __forceinline__ void block_exclusive_scan(int n) {
-  __shared__ uint32_t warp_sums[kWarps];
-  uint32_t* counts = (uint32_t*)dyn_smem();
-  const int per = (n + kThreads - 1) / kThreads;
-  const int beg = threadIdx.x * per;
-  uint32_t local = 0;
-  for (int i = 0; i < per; ++i)
-    if (beg + i < n) local += counts[beg + i];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t x = local;
-  for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
-    if (lane >= off) x += y;
-  }
-  if (lane == 31) warp_sums[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t s = lane < kWarps ? warp_sums[lane] : 0u;
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, s, off);
-      if (lane >= off) s += y;
-    }
-    if (lane < kWarps) warp_sums[lane] = s;
-  }
-  __syncthreads();
-  uint32_t run = (warp ? warp_sums[warp - 1] : 0u) + x - local;
-  for (int i = 0; i < per; ++i) {
-    if (beg + i < n) {
-      const uint32_t v = counts[beg + i];
-      counts[beg + i] = run;
-      run += v;
-    }
-  }
-  __syncthreads();
 }
 
 // Packed pair of floats as one 64-bit register for fma.rn.f32x2.
@@ -255,26 +217,27 @@ __device__ __forceinline__ void stage_table(const T* __restrict__ src, int os, i
 
 // Decodes the records grecs[c0, c0 + m) of one segment into the shared array the caller's
 // `emit(slot, rec, idx)` writes, in their order (the plan has sorted every bin by footprint
-// origin, and a segment's bins follow one another). Each thread takes kSortPer consecutive
+// origin, and a segment's bins follow one another). Each thread takes PER consecutive
 // records, all loads in flight together. With `index` (a gridding plan's visibility index per
 // record, partner flag in bit 31) the Hermitian partners are left out and the others close up.
 // Returns the number of records decoded.
-// warp_sums: kWarps words of shared memory for the prefix sum.
-template <class Emit>
+// NT threads (the CTA); warp_sums: NT / 32 words of shared memory for the prefix sum.
+template <int NT, int PER, class Emit>
 __device__ __forceinline__ int decode_chunk(const uint4* __restrict__ grecs, const uint32_t* __restrict__ index,
                                             uint32_t c0, int m, uint32_t* warp_sums, Emit emit) {
-  uint4 rec[kSortPer];
-  uint32_t idx[kSortPer];
-  const int first = threadIdx.x * kSortPer;
+  constexpr int kW = NT / 32;
+  uint4 rec[PER];
+  uint32_t idx[PER];
+  const int first = threadIdx.x * PER;
   int count = 0;
 #pragma unroll
-  for (int u = 0; u < kSortPer; ++u) {
+  for (int u = 0; u < PER; ++u) {
     const int i = min(first + u, m - 1);            // m >= 1: loads past the chunk repeat its last record
     rec[u] = __ldcs(grecs + c0 + i);
     idx[u] = index ? index[c0 + i] : 0u;
   }
 #pragma unroll
-  for (int u = 0; u < kSortPer; ++u) count += (first + u < m && !(idx[u] >> 31)) ? 1 : 0;
+  for (int u = 0; u < PER; ++u) count += (first + u < m && !(idx[u] >> 31)) ? 1 : 0;
   // exclusive prefix of the threads' counts
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t x = (uint32_t)count;
@@ -285,18 +248,18 @@ __device__ __forceinline__ int decode_chunk(const uint4* __restrict__ grecs, con
   if (lane == 31) warp_sums[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    uint32_t v = lane < kWarps ? warp_sums[lane] : 0u;
+    uint32_t v = lane < kW ? warp_sums[lane] : 0u;
     for (int off = 1; off < 32; off <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, v, off);
       if (lane >= off) v += y;
     }
-    if (lane < kWarps) warp_sums[lane] = v;
+    if (lane < kW) warp_sums[lane] = v;
   }
   __syncthreads();
   int pos = (int)((warp ? warp_sums[warp - 1] : 0u) + x) - count;
-  const int kept = (int)warp_sums[kWarps - 1];
+  const int kept = (int)warp_sums[kW - 1];
 #pragma unroll
-  for (int u = 0; u < kSortPer; ++u) {
+  for (int u = 0; u < PER; ++u) {
     if (first + u < m && !(idx[u] >> 31)) {
       emit(pos, rec[u], idx[u]);
       ++pos;
