@@ -56,6 +56,14 @@ extern "C" {
 #define WP_HERMITIAN_PAIRS 2  /* also grid each sample as W*conj(V) at -uvw */
 #define WP_KEEP_BINNING    4  /* wp_grid: keep this call's binning for wp_degrid_last (one more
                                  4-byte store per gridded visibility: its visibility index) */
+#define WP_COMPENSATED     8  /* wp_grid: compensated float32 accumulation of the grid. Every
+                                 addition of a footprint's partial sums into a cell returns the
+                                 cell's previous value, and the exact rounding error of that
+                                 float32 addition (TwoSum) is summed into a context-owned
+                                 compensation grid, added to the grid at the end: the cell then
+                                 carries the float32 rounding of its sum rather than the rounding
+                                 errors of all its additions. Slower (the atomics return); supports
+                                 up to 32 only (WP_EINVAL otherwise). */
 
 typedef struct wp_ctx wp_ctx;
 

@@ -12,7 +12,7 @@ fallback: if libwproj.so is missing, importing the binding raises.
 from __future__ import annotations
 
 from ._abi import (  # noqa: F401
-    LIB_PATH, PHASES, WP_ACCUMULATE, WP_EINVAL, WP_ESTATE, WP_HERMITIAN_PAIRS, WP_KEEP_BINNING, WP_OK, WP_TABLE_BF16, WP_TABLE_F16,
+    LIB_PATH, PHASES, WP_ACCUMULATE, WP_COMPENSATED, WP_EINVAL, WP_ESTATE, WP_HERMITIAN_PAIRS, WP_KEEP_BINNING, WP_OK, WP_TABLE_BF16, WP_TABLE_F16,
     WP_TABLE_F32, WBatch, WProj,
     WProjError, lib, probe_fp32_fma, taper_eval_host,
 )

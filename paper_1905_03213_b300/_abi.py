@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(_HERE, "libwproj.so")
 
 WP_OK, WP_EINVAL, WP_ENOMEM, WP_ECUDA, WP_EOVERFLOW, WP_ESTATE = range(6)
 WP_TABLE_F32, WP_TABLE_F16, WP_TABLE_BF16 = 0, 1, 2
-WP_ACCUMULATE, WP_HERMITIAN_PAIRS, WP_KEEP_BINNING = 1, 2, 4
+WP_ACCUMULATE, WP_HERMITIAN_PAIRS, WP_KEEP_BINNING, WP_COMPENSATED = 1, 2, 4, 8
 _TABLES = {"f32": WP_TABLE_F32, "f16": WP_TABLE_F16, "bf16": WP_TABLE_BF16}
 
 # every function declared in include/wproj.h
@@ -163,9 +163,11 @@ class WProj:
         self._check(lib.wp_make_wkernels(self._h, self._stream(stream)), "wp_make_wkernels")
 
     def grid(self, uvw, freq, vis, weight=None, grid=None, sum_w=None, n_dropped=None,
-             hermitian_pairs: bool = False, accumulate: bool = False, keep_binning: bool = False, stream=None):
+             hermitian_pairs: bool = False, accumulate: bool = False, keep_binning: bool = False,
+             compensated: bool = False, stream=None):
         """Returns (grid [N, N] complex64, sum_w [1] float64, n_dropped [1] int64), device tensors.
-        keep_binning: keep the binning for degrid_last (WP_KEEP_BINNING)."""
+        keep_binning: keep the binning for degrid_last (WP_KEEP_BINNING); compensated: compensated
+        float32 accumulation of the grid (WP_COMPENSATED)."""
         import torch
         dev = torch.device("cuda", self.device)
         _dev_tensor(uvw, torch.float64, "uvw")
@@ -183,7 +185,7 @@ class WProj:
         if n_dropped is None:
             n_dropped = torch.zeros(1, dtype=torch.int64, device=dev)
         flags = ((WP_ACCUMULATE if accumulate else 0) | (WP_HERMITIAN_PAIRS if hermitian_pairs else 0)
-                 | (WP_KEEP_BINNING if keep_binning else 0))
+                 | (WP_KEEP_BINNING if keep_binning else 0) | (WP_COMPENSATED if compensated else 0))
         self._last_grid_shape = None
         self._check(lib.wp_grid(self._h, _ptr(uvw), _ptr(freq), _ptr(vis), _ptr(weight), nrow, nchan, flags,
                                 _ptr(grid), _ptr(sum_w), _ptr(n_dropped), self._stream(stream)), "wp_grid")

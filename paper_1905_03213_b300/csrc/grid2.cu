@@ -41,6 +41,7 @@ struct G2Args {
   const unsigned char* lanetab;   // lane-order tables of the planes with S > 16 (global)
   const int64_t* lanetab_off;     // [Nw] byte offset of each plane in lanetab (-1: none)
   float2* grid;
+  float2* comp;             // compensated accumulation: the rounding errors of the grid's sums, or nullptr
   int smem_bytes;           // dynamic shared memory of the launch
   int group_tiles;          // origin tiles of one tile row sorted as one segment, at most
   int nunits;               // work units (equal shares of the estimated work)
@@ -81,10 +82,25 @@ struct Footprint {
   }
   // Adds this lane's cells to the grid where `pred`: rows r < nrow of its column, the first at
   // cell index idx (32-bit: n <= 32768), the next ones n cells apart. Predicated, no branch.
-  __device__ __forceinline__ void flush(bool pred, float2* __restrict__ grid, uint32_t idx, uint32_t n, int nrow) const {
+  __device__ __forceinline__ void flush(bool pred, float2* __restrict__ grid, float2* __restrict__ comp, uint32_t idx,
+                                        uint32_t n, int nrow) const {
+    if (!comp) {
+#pragma unroll
+      for (int r = 0; r < L::R; ++r) {
+        red_add2_if(pred && r < nrow, grid + idx, lo_of(p1[r]) + hi_of(p1[r]), lo_of(p2[r]) + hi_of(p2[r]));
+        idx += n;
+      }
+      return;
+    }
+    // compensated: each addition returns the cell's previous value, and the exact rounding error
+    // of old + x (TwoSum) goes to the compensation grid
 #pragma unroll
     for (int r = 0; r < L::R; ++r) {
-      red_add2_if(pred && r < nrow, grid + idx, lo_of(p1[r]) + hi_of(p1[r]), lo_of(p2[r]) + hi_of(p2[r]));
+      if (pred && r < nrow) {
+        const float x = lo_of(p1[r]) + hi_of(p1[r]), y = lo_of(p2[r]) + hi_of(p2[r]);
+        const float2 old = atom_add2(grid + idx, x, y);
+        red_add2(comp + idx, two_sum_err(old.x, x), two_sum_err(old.y, y));
+      }
       idx += n;
     }
   }
@@ -136,6 +152,7 @@ __device__ __forceinline__ void warp_grid(const G2Args& a, int tab_off, const un
   uint2* hdr = (uint2*)(dyn_smem() + ring_off + 16 * kRingRecs);
   const uint4* grecs = (const uint4*)a.recs;
   float2* __restrict__ grid = a.grid;
+  float2* __restrict__ comp = a.comp;
   const uint32_t n = (uint32_t)a.g.n;
   const int os = a.g.os;
   // batches: taken from the CTA's counter (next != nullptr), or the one static piece
@@ -185,7 +202,7 @@ __device__ __forceinline__ void warp_grid(const G2Args& a, int tab_off, const un
         const int d = i0 - ci0;
         const bool slide = j0 == cj0 && (unsigned)(d - 1) < (unsigned)(S - 1);   // 0 < d < S on the same row
         const bool keep = slide && ac >= d;
-        fp.flush(cz != kNoOrigin && !keep, grid, cidx, n, nrow);
+        fp.flush(cz != kNoOrigin && !keep, grid, comp, cidx, n, nrow);
         if (slide) {
           fp.keep_if(keep);
           ac = keep ? ac - d : ac - d + S;
@@ -214,7 +231,7 @@ __device__ __forceinline__ void warp_grid(const G2Args& a, int tab_off, const un
     }
     if (nb >= ne) break;
     if (nb != ce) {                                        // not the continuation of this batch
-      fp.flush(cz != kNoOrigin, grid, cidx, n, nrow);
+      fp.flush(cz != kNoOrigin, grid, comp, cidx, n, nrow);
       fp.zero();
       cz = kNoOrigin;
       cj0 = -1;
@@ -224,7 +241,7 @@ __device__ __forceinline__ void warp_grid(const G2Args& a, int tab_off, const un
     q = cb;
     grab(nb, ne);
   }
-  fp.flush(cz != kNoOrigin, grid, cidx, n, nrow);
+  fp.flush(cz != kNoOrigin, grid, comp, cidx, n, nrow);
 }
 
 // The records [pb, pe) of plane p (support S) with the whole CTA: stage the plane's table
@@ -420,6 +437,7 @@ cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used
   a.lanetab = (const unsigned char*)ctx->d_lanetab;
   a.lanetab_off = ctx->d_lanetab_off;
   a.grid = grid;
+  a.comp = ctx->comp_active;
   a.smem_bytes = (int)smem;
   a.group_tiles = group;
   a.nunits = ctx->nsm * kUnitsPerCta;
@@ -452,6 +470,24 @@ namespace wp {
 
 size_t grid_job_desc_bytes() { return sizeof(G2Args); }
 
+namespace {
+// grid += comp, elementwise (the compensated accumulation's last step).
+__global__ void k_add_comp(float2* __restrict__ grid, const float2* __restrict__ comp, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 c = comp[i];
+    float2 g = grid[i];
+    g.x += c.x;
+    g.y += c.y;
+    grid[i] = g;
+  }
+}
+}  // namespace
+
+cudaError_t launch_add_comp(float2* grid, const float2* comp, int64_t n, int nsm, cudaStream_t s) {
+  k_add_comp<<<nsm * 8, 256, 0, s>>>(grid, comp, n);
+  return cudaGetLastError();
+}
+
 // Host-side arguments of one job for the multi-job launch (job's context, grid and the launch's
 // shared-memory size); the job's own work-estimate scan must have run before the launch.
 void grid_job_desc(wp_ctx* ctx, float2* grid, size_t smem, void* out) {
@@ -468,6 +504,7 @@ void grid_job_desc(wp_ctx* ctx, float2* grid, size_t smem, void* out) {
   a.lanetab = (const unsigned char*)ctx->d_lanetab;
   a.lanetab_off = ctx->d_lanetab_off;
   a.grid = grid;
+  a.comp = nullptr;
   a.smem_bytes = (int)smem;
   a.group_tiles = group;
   a.nunits = 0;

@@ -157,6 +157,8 @@ struct wp_ctx {
   wp::DeviceBuffer rec_index2;         // the origin sort's output for rec_index
   uint32_t* d_binlist = nullptr;       // [nbins] the non-empty bins (origin sort work list)
   uint32_t* d_binwork = nullptr;       // [4]: list lengths (large, other bins), next entry, finished CTAs
+  wp::DeviceBuffer comp;               // [N][N] float2: rounding errors of a compensated wp_grid
+  float2* comp_active = nullptr;       // set for the duration of a compensated wp_grid call
   bool have_grid_plan = false;         // records/rec_index hold the last wp_grid's binning
   int64_t plan_nrow = 0;
   int32_t plan_nchan = 0;
@@ -194,6 +196,8 @@ cudaError_t launch_grid(wp_ctx* ctx, float2* grid, cudaStream_t s);
 cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used);
 // shared memory the warp gridding kernel needs for ctx (0: outside its limits)
 size_t grid_v2_smem(const wp_ctx* ctx, int* group_tiles);
+// grid += comp (the last step of a compensated gridding call; grid2.cu)
+cudaError_t launch_add_comp(float2* grid, const float2* comp, int64_t n, int nsm, cudaStream_t s);
 // lane-order global tables of the planes with S > 16 (grid2.cu)
 size_t lane_table_bytes(int s, int os, int table_type);
 cudaError_t launch_lane_tables(wp_ctx* ctx, cudaStream_t s);

@@ -134,6 +134,24 @@ __device__ __forceinline__ void red_add2(float2* p, float x, float y) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(x), "f"(y) : "memory");
 }
 
+// Atomic addition of two floats into global memory returning the previous values (one vector
+// atomic, rounded to nearest like the reduction).
+__device__ __forceinline__ float2 atom_add2(float2* p, float x, float y) {
+  float2 old;
+  asm volatile("atom.global.v2.f32.add {%0, %1}, [%2], {%3, %4};" : "=f"(old.x), "=f"(old.y) : "l"(p), "f"(x), "f"(y)
+               : "memory");
+  return old;
+}
+
+// The rounding error e of s = fl(a + b), so that a + b = s + e exactly (Knuth's TwoSum: six
+// additions in round-to-nearest, no ordering of |a| and |b| needed).
+__device__ __forceinline__ float two_sum_err(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  const float av = __fsub_rn(s, bv);
+  return __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
 // red_add2 where p is true: one predicated instruction, no branch.
 __device__ __forceinline__ void red_add2_if(bool pred, float2* p, float x, float y) {
   asm volatile(

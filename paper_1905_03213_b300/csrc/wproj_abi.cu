@@ -193,7 +193,7 @@ void wp_destroy(wp_ctx* ctx) {
                   ctx->d_wplane,   ctx->d_tab_off,   ctx->d_tab64_off, ctx->d_quad_off, ctx->d_nu,
                   ctx->d_counts,   ctx->d_offsets,   ctx->d_cursor,    ctx->d_partials, ctx->d_chan,
                   ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2, ctx->d_work, ctx->rounded.ptr, ctx->rec_index.ptr, ctx->d_suboff, ctx->d_lanetab, ctx->d_lanetab_off,
-                  ctx->coord_scratch.ptr, ctx->bl_scratch.ptr, ctx->records2.ptr, ctx->rec_index2.ptr,
+                  ctx->coord_scratch.ptr, ctx->bl_scratch.ptr, ctx->records2.ptr, ctx->rec_index2.ptr, ctx->comp.ptr,
                   ctx->d_binlist, ctx->d_binwork};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -374,8 +374,15 @@ int wp_make_wkernels(wp_ctx* ctx, void* stream) {
 int wp_grid(wp_ctx* ctx, const double* uvw, const double* freq, const void* vis, const float* weight, int64_t nrow,
             int32_t nchan, int32_t flags, void* grid, double* sum_w, int64_t* n_dropped, void* stream) {
   if (!ctx) return WP_EINVAL;
-  if (flags & ~(WP_ACCUMULATE | WP_HERMITIAN_PAIRS | WP_KEEP_BINNING)) return fail(ctx, WP_EINVAL, "unknown flag bits");
+  if (flags & ~(WP_ACCUMULATE | WP_HERMITIAN_PAIRS | WP_KEEP_BINNING | WP_COMPENSATED))
+    return fail(ctx, WP_EINVAL, "unknown flag bits");
   const bool keep = (flags & WP_KEEP_BINNING) != 0;
+  const bool compensated = (flags & WP_COMPENSATED) != 0;
+  if (compensated) {
+    int group = 1;
+    if (!wp::grid_v2_smem(ctx, &group))
+      return fail(ctx, WP_EINVAL, "WP_COMPENSATED needs the register-accumulating kernel (supports up to 32)");
+  }
   if (!grid) return fail(ctx, WP_EINVAL, "grid must not be NULL");
   if (nrow > 0 && !vis) return fail(ctx, WP_EINVAL, "vis must not be NULL");
   const int pairs = (flags & WP_HERMITIAN_PAIRS) ? 1 : 0;
@@ -384,6 +391,10 @@ int wp_grid(wp_ctx* ctx, const double* uvw, const double* freq, const void* vis,
   if (rc) return rc;
   const int32_t n = ctx->prm.n;
   if (!(flags & WP_ACCUMULATE)) WP_CUDA(ctx, cudaMemsetAsync(grid, 0, sizeof(float2) * (size_t)n * n, s));
+  if (compensated) {
+    if ((rc = ensure_buffer(ctx, ctx->comp, sizeof(float2) * (size_t)n * n, "compensation grid"))) return rc;
+    WP_CUDA(ctx, cudaMemsetAsync(ctx->comp.ptr, 0, sizeof(float2) * (size_t)n * n, s));
+  }
   {
     Phase ph(ctx, WP_PHASE_PLAN, s);
     WP_CUDA(ctx, wp::launch_plan(ctx, uvw, (const float2*)vis, weight, nrow, nchan, pairs != 0, false, keep, s));
@@ -393,7 +404,14 @@ int wp_grid(wp_ctx* ctx, const double* uvw, const double* freq, const void* vis,
   ctx->plan_nchan = nchan;
   {
     Phase ph(ctx, WP_PHASE_GRID, s);
-    WP_CUDA(ctx, wp::launch_grid(ctx, (float2*)grid, s));
+    ctx->comp_active = compensated ? (float2*)ctx->comp.ptr : nullptr;
+    const cudaError_t eg = wp::launch_grid(ctx, (float2*)grid, s);
+    ctx->comp_active = nullptr;
+    WP_CUDA(ctx, eg);
+    if (compensated) {
+      WP_CUDA(ctx, wp::launch_add_comp((float2*)grid, (const float2*)ctx->comp.ptr, (int64_t)n * n, ctx->nsm, s));
+      ++ctx->launches;
+    }
   }
   if (sum_w || n_dropped) {
     k_store_scalars<<<1, 1, 0, s>>>(ctx->d_wsum, ctx->d_dropped, sum_w, (long long*)n_dropped,
