@@ -150,7 +150,6 @@ struct wp_ctx {
   int32_t max_chan = 0;
   wp::DeviceBuffer records;
   wp::DeviceBuffer records2;           // the origin sort's output; swapped with records after it
-  wp::DeviceBuffer rounded;            // [3][nvis] int32 rounded coordinates (plan scratch)
   wp::DeviceBuffer coord_scratch;      // wp_grid_baseline: [ngridded][8] int32 coordinates
   wp::DeviceBuffer bl_scratch;         // wp_baseline_order: row baseline indices, counts, cursors
   wp::DeviceBuffer rec_index;          // [records] uint32: visibility index | partner << 31 (wp_grid)

@@ -1,15 +1,18 @@
-// Coordinates (float64) and binning of visibilities by (w-plane, footprint-origin tile).
+// Coordinates (float64 definition) and binning of visibilities by (w-plane, footprint-origin
+// tile).
 //
 // Coordinates follow the W-projection gridding step (Sec. 2.1/2.2 of Lao et al. 2019: each
-// visibility lands on the uv grid through a C_full x C_full kernel); the arithmetic is
-// float64 and round-half-to-even, in the order written in wproj.h, so that the integer
+// visibility lands on the uv grid through a C_full x C_full kernel); they are defined by float64
+// products and round-half-to-even, in the order written in wproj.h, so that the integer
 // decisions (oversampled position, plane, footprint) are the same on every platform that
-// evaluates the same IEEE float64 operations.
+// evaluates the same IEEE float64 operations. The kernels reach that definition through a
+// float32 evaluation with a proven error bound and form the float64 products only where the
+// bound leaves the rounding undecided.
 //
 // Binning is a counting sort: a histogram of bin keys, an exclusive prefix sum giving each
 // bin's start index (the construction of Eq. 6, there applied to baselines), and a scatter
-// that writes each visibility's 16-byte record into its bin. Records within a bin are in
-// no particular order.
+// that writes each visibility's 16-byte record into its bin; a last pass sorts each bin's
+// records by footprint origin.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,25 +61,6 @@ struct Rounded {
   bool fin, wpos, wneg;
 };
 
-// Scratch form of Rounded: u, v and plane | fin << 16 | wpos << 17 | wneg << 18, stored as
-// three arrays of nvis int32.
-__device__ __forceinline__ void store_rounded(int32_t* __restrict__ out, int64_t nvis, int64_t k, const Rounded& r) {
-  out[k] = r.u;
-  out[nvis + k] = r.v;
-  out[2 * nvis + k] = r.plane | (r.fin ? 1 << 16 : 0) | (r.wpos ? 1 << 17 : 0) | (r.wneg ? 1 << 18 : 0);
-}
-__device__ __forceinline__ Rounded load_rounded(const int32_t* __restrict__ in, int64_t nvis, int64_t k) {
-  Rounded r;
-  r.u = in[k];
-  r.v = in[nvis + k];
-  const int32_t f = in[2 * nvis + k];
-  r.plane = f & 0xffff;
-  r.fin = (f >> 16) & 1;
-  r.wpos = (f >> 17) & 1;
-  r.wneg = (f >> 18) & 1;
-  return r;
-}
-
 __device__ __forceinline__ Rounded round_coords(double ux, double vy, double wz, double w_m, const Geometry& g) {
   Rounded r;
   const unsigned long long bx = abs_bits(ux), by = abs_bits(vy), bz = abs_bits(wz);
@@ -122,25 +106,82 @@ __device__ __forceinline__ uint32_t bin_of(const Coord& c, const Geometry& g) {
                     g.div_tx.div((uint32_t)c.i0));
 }
 
-// Per-(row, channel) products, shared by the visibility and its Hermitian partner.
-struct Products {
-  double ux, vy, wz, w;
-};
+// ---- the rounded coordinates of one visibility, float32 first ----
+//
+// B300 issues float64 arithmetic at a small fraction of its float32 rate (a few operations per
+// SM and clock), and three float64 products per visibility made the histogram pass bound by
+// that pipe. The products are therefore first formed in float32 from truncated operands, whose
+// distance to the float64 product is bounded; where that bound cannot carry the product across
+// a rounding boundary (a half-integer), the rint of the float32 value is the rint of the
+// float64 product. Only the remaining visibilities (within about 1e-6 |x| of a boundary, and
+// any operand out of range, infinite or NaN) form the float64 products. Either way the result
+// is the float64 definition above, bit for bit.
 
-__device__ __forceinline__ Products products(const double* __restrict__ uvw, const double* __restrict__ chan,
-                                             int64_t k, int32_t nchan) {
-  const uint32_t r = (uint32_t)k / (uint32_t)nchan;    // nvis < 2^32 (32-bit record offsets)
-  const int32_t ch = (int32_t)((uint32_t)k - r * (uint32_t)nchan);
-  const double u = uvw[3 * (size_t)r], v = uvw[3 * (size_t)r + 1], w = uvw[3 * (size_t)r + 2];
-  const double kx = chan[2 * ch], kw = chan[2 * ch + 1];
-  Products p;
-  p.ux = __dmul_rn(u, kx);
-  p.vy = __dmul_rn(v, kx);
-  p.wz = __dmul_rn(__longlong_as_double(__double_as_longlong(w) & 0x7fffffffffffffffll), kw);
-  p.w = w;
-  return p;
+// float32 of a float64 with its significand truncated, from the bit pattern (no float64
+// instruction): |f - x| < 2^-23 |x| for 2^-126 <= |x| < 2^128, and +-0 for |x| < 2^-126. The
+// callers take it only for biased exponents <= 1086 (|x| < 2^64).
+__device__ __forceinline__ float trunc_float(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  const uint32_t sign = hi & 0x80000000u;
+  return __uint_as_float(e < 897u ? sign : sign | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ uint32_t exp_of(double x) {
+  return (uint32_t)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ffu;
 }
 
+// n = rint(p) for the float64 product p of two operands whose truncated float32 product is X,
+// when that is decided: |X - p| < 3e-7 |X| + 2^-62 (two truncations below 2^-23 each, the
+// float32 product's rounding 2^-24 and the float64 product's 2^-53, relative; an operand
+// flushed to zero contributes below 2^-62), so p lies within `margin` of X, and when the
+// half-integers nearest X are farther than that, p rounds to the same integer as X.
+__device__ __forceinline__ bool rint_decided(float X, int32_t& n) {
+  const float ax = fabsf(X);
+  const float r = rintf(X);
+  const float margin = fmaf(ax, 0x1p-20f, 0x1p-40f);
+  n = (int32_t)r;
+  return ax < 0x1p28f && 0.5f - fabsf(X - r) > margin;
+}
+
+// The rounded coordinates of visibility k (row k / nchan, channel k % nchan).
+__device__ __forceinline__ Rounded rounded_coords(const double* __restrict__ uvw, const double* __restrict__ chan,
+                                                  int64_t k, const FastDiv& nchan, const Geometry& g) {
+  const uint32_t row = nchan.div((uint32_t)k);         // nvis < 2^32 (32-bit record offsets)
+  const int32_t ch = (int32_t)((uint32_t)k - row * nchan.d);
+  const double u = uvw[3 * (size_t)row], v = uvw[3 * (size_t)row + 1], w = uvw[3 * (size_t)row + 2];
+  const double kx = chan[2 * ch], kw = chan[2 * ch + 1];
+  const double aw = __longlong_as_double(__double_as_longlong(w) & 0x7fffffffffffffffll);
+  const uint32_t ekx = exp_of(kx), ekw = exp_of(kw);
+  bool done = exp_of(u) <= 1086u && exp_of(v) <= 1086u && exp_of(aw) <= 1086u && ekx >= 897u && ekx <= 1086u &&
+              ekw >= 897u && ekw <= 1086u;
+  Rounded r;
+  if (done) {
+    const float fkx = trunc_float(kx);
+    int32_t nu, nv, np;
+    done = rint_decided(trunc_float(u) * fkx, nu) && rint_decided(trunc_float(v) * fkx, nv) &&
+           rint_decided(trunc_float(aw) * trunc_float(kw), np);
+    r.u = nu;
+    r.v = nv;
+    r.plane = min(g.n_w - 1, np);
+    r.fin = true;
+    const unsigned long long bw = (unsigned long long)__double_as_longlong(w);
+    r.wpos = (bw >> 63) == 0 && (bw << 1) != 0;
+    r.wneg = (bw >> 63) != 0 && (bw << 1) != 0;
+  }
+  if (!done) r = round_coords(__dmul_rn(u, kx), __dmul_rn(v, kx), __dmul_rn(aw, kw), w, g);
+  return r;
+}
+
+// Adds x to the float32 pair (hi, lo) whose sum carries a running total: TwoSum (Knuth) puts
+// the exact rounding error of hi + x into lo, so the pair stays within a few 2^-48 of the exact
+// sum over a thread's handful of terms.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
 
 __global__ void k_channel_factors(const double* __restrict__ freq, int32_t nchan, double os_l,
                                   double wscale, double* __restrict__ out) {
@@ -181,28 +222,25 @@ __device__ __forceinline__ void hash_clear(uint32_t* keys, uint32_t* cnt) {
   }
 }
 
-// Pass 1: bin histogram, dropped count and kept-weight sum; optionally the rounded
-// coordinates of every visibility for pass 3.
+// Pass 1: bin histogram, dropped count and kept-weight sum.
 __global__ void __launch_bounds__(kPlanThreads) k_histogram(const double* __restrict__ uvw,
                                                             const double* __restrict__ chan,
                                                             const float* __restrict__ weight, int64_t nvis,
-                                                            int32_t nchan, int32_t pairs, Geometry g,
+                                                            FastDiv nchan, int32_t pairs, Geometry g,
                                                             uint32_t* __restrict__ counts,
                                                             unsigned long long* __restrict__ dropped,
-                                                            double* __restrict__ wsum, int32_t* __restrict__ rounded) {
+                                                            double* __restrict__ wsum) {
   __shared__ uint32_t keys[kHashSlots], cnt[kHashSlots];
   hash_clear(keys, cnt);
   __syncthreads();
-  double my_w = 0.0;
-  unsigned long long my_drop = 0;
+  float w_hi = 0.f, w_lo = 0.f;                             // kept-weight sum as a float32 pair
+  uint32_t my_drop = 0;
   const int64_t base = (int64_t)blockIdx.x * kPlanVis;
 #pragma unroll
   for (int u = 0; u < kPlanPer; ++u) {
     const int64_t k = base + u * kPlanThreads + threadIdx.x;
     if (k >= nvis) break;
-    const Products pr = products(uvw, chan, k, nchan);
-    const Rounded rd = round_coords(pr.ux, pr.vy, pr.wz, pr.w, g);
-    if (rounded) store_rounded(rounded, nvis, k, rd);
+    const Rounded rd = rounded_coords(uvw, chan, k, nchan, g);
     int nkept = 0;
     for (int h = 0; h <= pairs; ++h) {
       const Coord c = make_coord(rd, h == 1, g);
@@ -214,22 +252,25 @@ __global__ void __launch_bounds__(kPlanThreads) k_histogram(const double* __rest
       }
       nkept += c.keep ? 1 : 0;
     }
-    my_drop += (unsigned long long)(pairs + 1 - nkept);
-    if (nkept) my_w = fma((double)(weight ? weight[k] : 1.0f), (double)nkept, my_w);
+    my_drop += (uint32_t)(pairs + 1 - nkept);
+    // weight x 1 or x 2 is exact in float32
+    if (nkept) pair_add(w_hi, w_lo, (weight ? weight[k] : 1.0f) * (float)nkept);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kHashSlots; i += kPlanThreads)
     if (keys[i] != kHashEmpty) atomicAdd(&counts[keys[i]], cnt[i]);
-  // block reduction of the two scalars
+  // block reduction of the two scalars: float32 pairs within a warp, float64 across warps
   __shared__ double sw[kPlanThreads / 32];
   __shared__ unsigned long long sd[kPlanThreads / 32];
   for (int off = 16; off > 0; off >>= 1) {
-    my_w += __shfl_xor_sync(0xffffffffu, my_w, off);
+    const float oh = __shfl_xor_sync(0xffffffffu, w_hi, off), ol = __shfl_xor_sync(0xffffffffu, w_lo, off);
+    pair_add(w_hi, w_lo, oh);
+    w_lo += ol;
     my_drop += __shfl_xor_sync(0xffffffffu, my_drop, off);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
-    sw[warp] = my_w;
+    sw[warp] = (double)w_hi + (double)w_lo;
     sd[warp] = my_drop;
   }
   __syncthreads();
@@ -245,32 +286,32 @@ __global__ void __launch_bounds__(kPlanThreads) k_histogram(const double* __rest
   }
 }
 
-// Pass 3: scatter records into their bins (coordinates from pass 1's scratch when given): each
+// Pass 3: scatter records into their bins (coordinates recomputed as in pass 1): each
 // record's rank among the CTA's records of its bin comes from the hash table's counter, then one
 // global atomic per bin reserves the CTA's run of slots, and the records go to run start + rank.
 __global__ void __launch_bounds__(kPlanThreads) k_scatter(const double* __restrict__ uvw, const double* __restrict__ chan,
                                                           const float2* __restrict__ vis, const float* __restrict__ weight,
-                                                          int64_t nvis, int32_t nchan, int32_t pairs, int32_t for_degrid,
+                                                          int64_t nvis, FastDiv nchan, int32_t pairs, int32_t for_degrid,
                                                           Geometry g, uint32_t* __restrict__ cursor,
-                                                          Record* __restrict__ records, const int32_t* __restrict__ rounded,
-                                                          uint32_t* __restrict__ index) {
+                                                          Record* __restrict__ records, uint32_t* __restrict__ index) {
   __shared__ uint32_t keys[kHashSlots], cnt[kHashSlots];
   hash_clear(keys, cnt);
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kPlanVis;
   Rounded rd[kPlanPer];
   uint32_t code[kPlanPer][2];                             // slot << 16 | rank, or 0xffffffff
+  float2 v[kPlanPer];                                     // loaded here, used after the barriers
+  float wt[kPlanPer];
 #pragma unroll
   for (int u = 0; u < kPlanPer; ++u) {
     const int64_t k = base + u * kPlanThreads + threadIdx.x;
     code[u][0] = code[u][1] = 0xffffffffu;
     if (k >= nvis) continue;
-    if (rounded) {
-      rd[u] = load_rounded(rounded, nvis, k);
-    } else {
-      const Products pr = products(uvw, chan, k, nchan);
-      rd[u] = round_coords(pr.ux, pr.vy, pr.wz, pr.w, g);
+    if (!for_degrid) {
+      v[u] = __ldcs(vis + k);
+      wt[u] = weight ? __ldcs(weight + k) : 1.0f;
     }
+    rd[u] = rounded_coords(uvw, chan, k, nchan, g);
     for (int h = 0; h <= pairs; ++h) {
       const Coord c = make_coord(rd[u], h == 1, g);
       if (c.keep) {
@@ -282,19 +323,26 @@ __global__ void __launch_bounds__(kPlanThreads) k_scatter(const double* __restri
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kHashSlots; i += kPlanThreads)
-    if (keys[i] != kHashEmpty) cnt[i] = atomicAdd(&cursor[keys[i]], cnt[i]);
+  {
+    // every reservation of this thread in flight before the first result is used
+    constexpr int kSlotsPer = kHashSlots / kPlanThreads;
+    uint32_t start[kSlotsPer];
+#pragma unroll
+    for (int j = 0; j < kSlotsPer; ++j) {
+      const int i = threadIdx.x + j * kPlanThreads;
+      const uint32_t key = keys[i];
+      start[j] = key != kHashEmpty ? atomicAdd(&cursor[key], cnt[i]) : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kSlotsPer; ++j) cnt[threadIdx.x + j * kPlanThreads] = start[j];
+  }
   __syncthreads();
 #pragma unroll
   for (int u = 0; u < kPlanPer; ++u) {
     const int64_t k = base + u * kPlanThreads + threadIdx.x;
     if (k >= nvis) continue;
     float2 val = make_float2(0.f, 0.f);
-    if (!for_degrid) {
-      const float2 v = vis[k];
-      const float wt = weight ? weight[k] : 1.0f;
-      val = make_float2(wt * v.x, wt * v.y);
-    }
+    if (!for_degrid) val = make_float2(wt[u] * v[u].x, wt[u] * v[u].y);
     for (int h = 0; h <= pairs; ++h) {
       if (code[u][h] == 0xffffffffu) continue;
       const Coord c = make_coord(rd[u], h == 1, g);
@@ -415,10 +463,9 @@ __global__ void k_bin_costs(const uint32_t* __restrict__ offsets, int64_t nbins,
 }
 
 __global__ void k_coords_out(const double* __restrict__ uvw, const double* __restrict__ chan, int64_t nvis,
-                             int32_t nchan, int32_t pairs, Geometry g, int32_t* __restrict__ out) {
+                             FastDiv nchan, int32_t pairs, Geometry g, int32_t* __restrict__ out) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nvis; k += (int64_t)gridDim.x * blockDim.x) {
-    const Products pr = products(uvw, chan, k, nchan);
-    const Rounded rd = round_coords(pr.ux, pr.vy, pr.wz, pr.w, g);
+    const Rounded rd = rounded_coords(uvw, chan, k, nchan, g);
     for (int h = 0; h <= pairs; ++h) {
       const Coord c = make_coord(rd, h == 1, g);
       int32_t* o = out + 8 * (k + h * nvis);
@@ -640,17 +687,16 @@ cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const
   if ((e = cudaMemsetAsync(ctx->d_dropped, 0, sizeof(unsigned long long), s))) return e;
   if ((e = cudaMemsetAsync(ctx->d_wsum, 0, sizeof(double), s))) return e;
   const unsigned plan_blocks = (unsigned)((nvis + kPlanVis - 1) / kPlanVis);
-  // pass 1 keeps the rounded coordinates for pass 3 when the context's scratch holds them
-  int32_t* rounded = ctx->rounded.bytes >= (size_t)nvis * 12 ? (int32_t*)ctx->rounded.ptr : nullptr;
+  const FastDiv fdiv = FastDiv::make((uint32_t)std::max<int32_t>(nchan, 1));
   // a gridding plan asked to keep its binning also records each record's visibility index, for
   // wp_degrid_last
   const size_t nrec = (size_t)nvis * (pairs ? 2 : 1);
   uint32_t* index = (keep_index && !for_degrid && ctx->rec_index.bytes >= nrec * 4) ? (uint32_t*)ctx->rec_index.ptr : nullptr;
   ctx->launches += 4 + (nvis > 0 ? 2 : 0);  // prefix sum (3), bin offsets, histogram and scatter
   if (nvis > 0) {
-    k_histogram<<<plan_blocks, kPlanThreads, 0, s>>>(uvw, ctx->d_chan, for_degrid ? nullptr : weight, nvis, nchan,
+    k_histogram<<<plan_blocks, kPlanThreads, 0, s>>>(uvw, ctx->d_chan, for_degrid ? nullptr : weight, nvis, fdiv,
                                                        pairs ? 1 : 0, ctx->geo, ctx->d_counts, ctx->d_dropped,
-                                                       ctx->d_wsum, rounded);
+                                                       ctx->d_wsum);
     if ((e = cudaGetLastError())) return e;
   }
   const int64_t tiles = (nsub + kScanTile - 1) / kScanTile;
@@ -665,9 +711,9 @@ cudaError_t launch_plan(wp_ctx* ctx, const double* uvw, const float2* vis, const
                                                                           ctx->d_offsets);
   if ((e = cudaGetLastError())) return e;
   if (nvis > 0) {
-    k_scatter<<<plan_blocks, kPlanThreads, 0, s>>>(uvw, ctx->d_chan, vis, weight, nvis, nchan, pairs ? 1 : 0,
+    k_scatter<<<plan_blocks, kPlanThreads, 0, s>>>(uvw, ctx->d_chan, vis, weight, nvis, fdiv, pairs ? 1 : 0,
                                                      for_degrid ? 1 : 0, ctx->geo, ctx->d_cursor,
-                                                     (Record*)ctx->records.ptr, rounded, index);
+                                                     (Record*)ctx->records.ptr, index);
     if ((e = cudaGetLastError())) return e;
   }
   // pass 4: every bin's records sorted by footprint origin, into the second record buffer, which
@@ -723,7 +769,8 @@ cudaError_t launch_coords(wp_ctx* ctx, const double* uvw, int64_t nrow, int32_t 
   const int64_t nvis = nrow * nchan;
   if (nvis == 0) return cudaSuccess;
   ++ctx->launches;
-  k_coords_out<<<grid_blocks(nvis, ctx->nsm), 256, 0, s>>>(uvw, ctx->d_chan, nvis, nchan, pairs ? 1 : 0, ctx->geo,
+  k_coords_out<<<grid_blocks(nvis, ctx->nsm), 256, 0, s>>>(uvw, ctx->d_chan, nvis, FastDiv::make((uint32_t)nchan),
+                                                            pairs ? 1 : 0, ctx->geo,
                                                             out);
   return cudaGetLastError();
 }

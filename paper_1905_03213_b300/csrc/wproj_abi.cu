@@ -135,7 +135,6 @@ int prepare_vis_call(wp_ctx* ctx, const double* uvw, const double* freq, int64_t
   const size_t ng = (size_t)nrow * nchan * (pairs ? 2 : 1);
   if ((rc = ensure_buffer(ctx, ctx->records, std::max<size_t>(ng, 1) * sizeof(wp::Record), "records"))) return rc;
   if ((rc = ensure_buffer(ctx, ctx->records2, std::max<size_t>(ng, 1) * sizeof(wp::Record), "sorted records"))) return rc;
-  if ((rc = ensure_buffer(ctx, ctx->rounded, std::max<size_t>((size_t)nrow * nchan, 1) * 12, "coordinate scratch"))) return rc;
   if (want_index && (rc = ensure_buffer(ctx, ctx->rec_index, std::max<size_t>(ng, 1) * 4, "record indices"))) return rc;
   if (want_index && (rc = ensure_buffer(ctx, ctx->rec_index2, std::max<size_t>(ng, 1) * 4, "sorted record indices"))) return rc;
   ctx->have_grid_plan = false;          // the records are about to be replaced
@@ -192,7 +191,7 @@ void wp_destroy(wp_ctx* ctx) {
                   ctx->d_stage,    ctx->d_quad,      ctx->d_tab64,     ctx->d_tab,      ctx->d_supp,
                   ctx->d_wplane,   ctx->d_tab_off,   ctx->d_tab64_off, ctx->d_quad_off, ctx->d_nu,
                   ctx->d_counts,   ctx->d_offsets,   ctx->d_cursor,    ctx->d_partials, ctx->d_chan,
-                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2, ctx->d_work, ctx->rounded.ptr, ctx->rec_index.ptr, ctx->d_suboff, ctx->d_lanetab, ctx->d_lanetab_off,
+                  ctx->records.ptr, ctx->d_dropped,  ctx->d_wsum,     ctx->d_costoff,  ctx->d_partials2, ctx->d_work, ctx->rec_index.ptr, ctx->d_suboff, ctx->d_lanetab, ctx->d_lanetab_off,
                   ctx->coord_scratch.ptr, ctx->bl_scratch.ptr, ctx->records2.ptr, ctx->rec_index2.ptr, ctx->comp.ptr,
                   ctx->d_binlist, ctx->d_binwork};
   for (void* p : ptrs)
@@ -758,7 +757,6 @@ int wp_batch_create(const wp_job* jobs, int32_t njobs, wp_batch** out) {
     const size_t nv = (size_t)j.nrow * j.nchan, ng = nv * (pairs ? 2 : 1);
     if ((rc = ensure_buffer(ctx, ctx->records, std::max<size_t>(ng, 1) * sizeof(wp::Record), "records"))) return rc;
     if ((rc = ensure_buffer(ctx, ctx->records2, std::max<size_t>(ng, 1) * sizeof(wp::Record), "sorted records"))) return rc;
-    if ((rc = ensure_buffer(ctx, ctx->rounded, std::max<size_t>(nv, 1) * 12, "coordinate scratch"))) return rc;
     b->jobs.push_back(j);
   }
   wp_ctx* c0 = jobs[0].ctx;

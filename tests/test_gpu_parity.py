@@ -57,6 +57,39 @@ def test_coords_edge_values(torch_cuda):
     np.testing.assert_array_equal(got[k, 3].astype(bool), crd["conj"][k])
 
 
+def test_coords_near_rounding_boundaries(torch_cuda):
+    """Products within 1e-12 .. 0.05 of a half-integer, on both sides, over the whole range of a
+    4096-cell grid: the float32-first evaluation must take the float64 decision in every case
+    (it forms the float64 product only where its error bound leaves the rounding undecided)."""
+    import torch
+    import paper_1905_03213_b300 as W
+    n, os_, n_w, w_max = 4096, 8, 64, 1500.0
+    cell = 1.0 / (n * 3.1)
+    p = oracle.Params(n=n, cell=cell, n_w=n_w, w_max=w_max, s_min=8, s_max=8, os=os_)
+    wp = W.WProj(n=n, cell=cell, n_w=n_w, w_max=w_max, support_min=8, support_max=8, oversample=os_)
+    wp.make_wkernels()
+    f = np.array([1.0e9, 1.234567e9, 1.4e9])
+    kx = f / oracle.C_LIGHT * (os_ * (n * cell))
+    kw = f / oracle.C_LIGHT * ((n_w - 1) / w_max)
+    rng = np.random.default_rng(31)
+    offs = np.array([0.0, 1e-12, 1e-9, 1e-7, 1e-6, 1e-5, 1e-4, 3e-3, 6e-3, 1e-2, 1.4e-2, 2e-2, 5e-2])
+    offs = np.concatenate([offs, -offs[1:]])
+    m = rng.integers(-16000, 16000, size=(400, offs.size))
+    x = (m + 0.5 + offs[None, :]).ravel()
+    mw = rng.integers(0, n_w - 1, size=x.size)
+    z = mw + 0.5 + rng.choice(offs, size=x.size)
+    c = rng.integers(0, f.size, size=x.size)          # the channel whose factors hit the boundary
+    uvw = np.stack([x / kx[c], x[::-1] / kx[c], np.where(rng.random(x.size) < 0.5, -1, 1) * z / kw[c]], axis=1)
+    got = wp.coords(torch.from_numpy(uvw).cuda(), torch.from_numpy(f).cuda()).cpu().numpy()
+    crd = oracle.coords(uvw, f, p)
+    for col, key in ((0, "U"), (1, "V"), (2, "plane"), (3, "conj")):
+        np.testing.assert_array_equal(got[:, col], crd[key].astype(np.int64), err_msg=key)
+    np.testing.assert_array_equal(got[:, 4].astype(bool), crd["keep"])
+    # the cases do straddle: both roundings of the nominal half-integer occur
+    ux = (uvw[:, 0:1] * kx[None, :]).ravel()
+    assert (np.rint(ux) > np.floor(ux)).any() and (np.rint(ux) == np.floor(ux)).any()
+
+
 # ---------------------------------------------------------------- kernel tables
 @pytest.mark.parametrize("which", ["parity", "range"])
 def test_wkernel_tables(torch_cuda, which):
