@@ -151,7 +151,8 @@ def run_gpu(args):
 
     def make(table):
         return W.WProj(n=cfg.n, cell=cfg.cell, n_w=cfg.n_w, w_max=ob.w_max, support_min=cfg.s_min,
-                       support_max=cfg.s_max, oversample=cfg.oversample, table=table, tile=tile, device=local)
+                       support_max=cfg.s_max, oversample=cfg.oversample, table=table, tile=tile, device=local,
+                       units_per_cta=args.units)
 
     def stepper(wp, compensated=False):
         def step():
@@ -246,7 +247,8 @@ def run_gpu(args):
         "dtype": "f32" if args.table == "f32" else f"f32 ({args.table} tables)",
         "data": "synthetic (seeded array/uvw/sky generators; values from 200 point sources + noise)",
         "config": {"workload": workload_name(args.config) + (f"; first {args.rows} rows only" if args.rows else ""),
-                   "table": args.table, "tile": args.tile or "default", "gridded_visibilities": kept,
+                   "table": args.table, "tile": args.tile or "default",
+                   "units_per_cta": args.units or "default", "gridded_visibilities": kept,
                    "degridded_visibilities": kept_degrid,
                    "l2": "inputs larger than L2 (0.4 GB fp32, 4.5 GB mixed); no flush",
                    "degrid": "wp_degrid_last: degrids the gridded samples with the gridding call's binning",
@@ -753,6 +755,7 @@ def main():
                          "scheme), fp32peak (the FMA probe)")
     ap.add_argument("--table", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--tile", default="", help="origin tile WxH, e.g. 64x32")
+    ap.add_argument("--units", type=int, default=0, help="work units per CTA of the grid/degrid schedule (0: default)")
     ap.add_argument("--cpu-vis", type=int, default=6_000_000, help="visibilities (rows x channels) in the CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

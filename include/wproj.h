@@ -80,6 +80,9 @@ typedef struct wp_params {
   int32_t tile_x;       /* origin-tile width for binning (cells); 0 = default */
   int32_t tile_y;       /* origin-tile height (cells); 0 = default */
   int32_t device;       /* CUDA device ordinal */
+  int32_t units_per_cta; /* schedule granularity of the gridding and degridding kernels: their
+                            estimated work is cut into units_per_cta x (SM count) work units that
+                            persistent CTAs take from a counter; 1..64, 0 = default (6) */
 } wp_params;
 
 /* Creates a context: validates `p`, derives the per-plane supports and w values, computes

@@ -40,7 +40,8 @@ class Params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("cell_rad", ctypes.c_double), ("n_w", ctypes.c_int32),
                 ("w_max", ctypes.c_double), ("support_min", ctypes.c_int32), ("support_max", ctypes.c_int32),
                 ("oversample", ctypes.c_int32), ("screen_m", ctypes.c_int32), ("table_type", ctypes.c_int32),
-                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("units_per_cta", ctypes.c_int32)]
 
 
 def _load():
@@ -124,13 +125,13 @@ class WProj:
 
     def __init__(self, n: int, cell: float, n_w: int, w_max: float, support_min: int, support_max: int,
                  oversample: int, screen_m: int = 0, table: str = "f32", tile: tuple[int, int] = (0, 0),
-                 device: int = 0):
+                 device: int = 0, units_per_cta: int = 0):
         self.n, self.cell, self.n_w, self.w_max = n, cell, n_w, w_max
         self.support_min, self.support_max, self.oversample = support_min, support_max, oversample
         self.table = table
         self.device = device
         prm = Params(n, cell, n_w, w_max, support_min, support_max, oversample, screen_m, _TABLES[table],
-                     tile[0], tile[1], device)
+                     tile[0], tile[1], device, units_per_cta)
         h = ctypes.c_void_p()
         rc = lib.wp_create(ctypes.byref(h), ctypes.byref(prm))
         if rc:

@@ -293,7 +293,7 @@ cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* out, const
   a.index = index;
   a.smem_bytes = (int)smem;
   a.group_tiles = group;
-  a.nunits = ctx->nsm * kUnitsPerCta;
+  a.nunits = ctx->nsm * ctx->prm.units_per_cta;
   a.work = ctx->d_work + 2;
   cudaError_t e;
   if ((e = launch_bin_costs(ctx, s))) return e;

@@ -440,7 +440,7 @@ cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used
   a.comp = ctx->comp_active;
   a.smem_bytes = (int)smem;
   a.group_tiles = group;
-  a.nunits = ctx->nsm * kUnitsPerCta;
+  a.nunits = ctx->nsm * ctx->prm.units_per_cta;
   a.work = ctx->d_work;
   cudaError_t e;
   if ((e = launch_bin_costs(ctx, s))) return e;

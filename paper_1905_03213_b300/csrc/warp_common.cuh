@@ -24,7 +24,6 @@ constexpr int kCountsBytes = ((kMaxKeys + 1) * 4 + 15) & ~15;  // shared-memory 
 constexpr int kMinChunk = 512;
 constexpr int kSortPer = 16;                                  // records per thread in one sort
 constexpr uint32_t kNoOrigin = 0xffffffffu;
-constexpr int kUnitsPerCta = 6;                              // work units per CTA, on average
 
 // Lane layout. For support S <= 16 the warp's lanes form G row groups of S lanes; lane
 // g*S + e holds rows g*R .. g*R + R - 1 of one footprint column. For 16 < S <= 32 (H = 2 row

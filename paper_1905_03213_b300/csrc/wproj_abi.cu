@@ -222,6 +222,8 @@ int wp_create(wp_ctx** out, const wp_params* p) {
     return fail(nullptr, WP_EINVAL, "table_type must be WP_TABLE_F32, _F16 or _BF16");
   if (q.tile_x < 0 || q.tile_y < 0 || q.tile_x > 1024 || q.tile_y > 1024)
     return fail(nullptr, WP_EINVAL, "tile sizes must be 0 (default) or 1..1024");
+  if (q.units_per_cta < 0 || q.units_per_cta > 64)
+    return fail(nullptr, WP_EINVAL, "units_per_cta must be 0 (default) or 1..64");
 
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || q.device < 0 || q.device >= ndev) {
@@ -233,6 +235,7 @@ int wp_create(wp_ctx** out, const wp_params* p) {
   ctx->prm = q;
   if (ctx->prm.tile_x == 0) ctx->prm.tile_x = 32;
   if (ctx->prm.tile_y == 0) ctx->prm.tile_y = 32;
+  if (ctx->prm.units_per_cta == 0) ctx->prm.units_per_cta = 6;
   ctx->m = q.screen_m ? q.screen_m : std::max(65, 4 * q.support_max + 1);
   auto bail = [&](int code, const std::string& msg) {
     g_create_error = msg;

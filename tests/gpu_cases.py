@@ -82,11 +82,11 @@ def oracle_results(case: Case):
     return crd, g, sw
 
 
-def make_wproj(case: Case, table="f32", tile=(0, 0)):
+def make_wproj(case: Case, table="f32", tile=(0, 0), units_per_cta=0):
     import paper_1905_03213_b300 as W
     p = case.prm
     w = W.WProj(n=p.n, cell=p.cell, n_w=p.n_w, w_max=p.w_max, support_min=p.s_min, support_max=p.s_max,
-                oversample=p.os, screen_m=p.m, table=table, tile=tile)
+                oversample=p.os, screen_m=p.m, table=table, tile=tile, units_per_cta=units_per_cta)
     w.make_wkernels()
     return w
 

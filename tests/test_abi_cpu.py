@@ -73,7 +73,7 @@ def test_library_taper_even_unit_and_rejects_bad_input():
 def _params(**kw):
     import paper_1905_03213_b300 as W
     base = dict(n=256, cell_rad=4.8e-5, n_w=16, w_max=4000.0, support_min=7, support_max=7, oversample=8,
-                screen_m=0, table_type=0, tile_x=0, tile_y=0, device=0)
+                screen_m=0, table_type=0, tile_x=0, tile_y=0, device=0, units_per_cta=0)
     base.update(kw)
     return W._abi.Params(**base)
 
@@ -82,6 +82,7 @@ def _params(**kw):
     dict(n=15), dict(n=8), dict(cell_rad=0.0), dict(cell_rad=float("nan")), dict(n_w=0), dict(w_max=0.0),
     dict(oversample=7), dict(oversample=0), dict(support_min=0), dict(support_min=9, support_max=8),
     dict(screen_m=64), dict(table_type=5), dict(tile_x=-1), dict(cell_rad=0.01, n=256),
+    dict(units_per_cta=-1), dict(units_per_cta=65),
 ])
 def test_create_rejects_invalid_parameters_on_host(bad):
     import paper_1905_03213_b300 as W

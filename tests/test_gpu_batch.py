@@ -133,3 +133,26 @@ def test_autotune_picks_a_measured_candidate(torch_cuda):
     _, g_ref, _ = oracle_results(case)
     e, _ = peak_rel(g_best.cpu().numpy(), g_ref)
     assert e < 1e-5, e
+
+
+def test_autotune_tile_and_schedule_granularity(torch_cuda):
+    torch = torch_cuda
+    from paper_1905_03213_b300.autotune import tune
+    case = random_case(n=256, nrow=3000, nchan=2, n_w=6, s_min=6, s_max=12, pairs=True)
+    uvw, f, vis, wt = to_dev(case)
+    p = case.prm
+    params = dict(n=p.n, cell=p.cell, n_w=p.n_w, w_max=p.w_max, support_min=p.s_min, support_max=p.s_max,
+                  oversample=p.os, screen_m=p.m)
+    tiles, units = ((16, 16), (32, 32)), (2, 6, 16)
+    best, timings = tune(params, uvw, f, vis, wt, hermitian_pairs=True, tiles=tiles, units=units, reps=2,
+                         with_degrid=True, use_cache=False)
+    assert best["tile"] in tiles and best["units_per_cta"] in units
+    # every tile at the default granularity, then every granularity at the best tile
+    assert set(timings) >= {(t, 6) for t in tiles} | {(min(timings, key=timings.get)[0], u) for u in units}
+    assert all(t > 0 for t in timings.values())
+    _, g_ref, _ = oracle_results(case)
+    for un in (1, best["units_per_cta"], 64):
+        wp = make_wproj(case, tile=best["tile"], units_per_cta=un)
+        g, _, _ = wp.grid(uvw, f, vis, wt, hermitian_pairs=True)
+        e, _ = peak_rel(g.cpu().numpy(), g_ref)
+        assert e < 1e-5, (un, e)
