@@ -744,6 +744,26 @@ def run_compare(args):
     }
 
 
+def run_autotune(args):
+    """--autotune: the autotuner's search (tile shape x work units per CTA) on the workload's own
+    visibilities, each candidate one gridding plus one degridding with the gridding plan."""
+    import torch
+    import synth
+    from paper_1905_03213_b300.autotune import tune
+
+    cfg = synth.config(args.config)
+    ob = synth.observe(cfg, device="cuda:0", rows=args.rows or None)
+    freq = torch.as_tensor(ob.freqs, dtype=torch.float64, device="cuda:0")
+    params = dict(n=cfg.n, cell=cfg.cell, n_w=cfg.n_w, w_max=ob.w_max, support_min=cfg.s_min,
+                  support_max=cfg.s_max, oversample=cfg.oversample, table=args.table)
+    best, t = tune(params, ob.uvw.contiguous(), freq, ob.vis.contiguous(), ob.weight.contiguous(),
+                   hermitian_pairs=cfg.hermitian_pairs, tiles=((32, 16), (32, 32), (64, 32), (64, 16)),
+                   units=(3, 4, 6, 8, 12), reps=max(args.steps, 1), with_degrid=True, use_cache=False)
+    return {"metric": "ms per wp_grid + wp_degrid_last, by tile shape and work units per CTA",
+            "config": {"workload": workload_name(args.config), "table": args.table},
+            "best": best, "ms": {f"{k[0][0]}x{k[0][1]}/{k[1]}": v for k, v in t.items()}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -765,10 +785,13 @@ def main():
     ap.add_argument("--rows", type=int, default=0, help="use only the first ROWS rows (profiling captures)")
     ap.add_argument("--jobs", type=int, default=64, help="--config batched: number of jobs")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="--config batched: visibility-count scale")
+    ap.add_argument("--autotune", action="store_true", help="run the tile/granularity autotuner on the workload")
     args = ap.parse_args()
     if args.impl != "reference":
         args.warmup = max(args.warmup, 3)
-    if args.config == "fp32peak" and args.impl != "reference":
+    if args.autotune and args.impl != "reference":
+        out = run_autotune(args)
+    elif args.config == "fp32peak" and args.impl != "reference":
         out = run_fp32peak(args)
     elif args.config == "batched" and args.impl != "reference":
         out = run_batched(args)
