@@ -33,7 +33,6 @@ constexpr int kDecodeScratch = 128;            // bytes of dynamic shared memory
 // against 24 warps with 8 records per thread and batches of 16.
 constexpr int kDegridThreadsSmall = 1024;
 constexpr int kDegridThreadsLarge = 512;
-constexpr int kSmallMaxS = 16;
 // records per thread in one decoded chunk
 __host__ __device__ constexpr int decode_per(int threads) { return threads == kDegridThreadsSmall ? 4 : 16; }
 
@@ -53,6 +52,7 @@ struct D2Args {
   int smem_bytes;
   int group_tiles;
   int nunits;
+  int64_t bin_lo, bin_hi;   // the bins this launch degrids (a prefix or suffix of the planes)
   uint32_t* work;           // [2]: next unit, finished CTAs (both zero between launches)
 };
 
@@ -239,7 +239,7 @@ __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
 
 template <class T, int NT>
 __global__ void __launch_bounds__(NT, 1) k_degrid_v2(D2Args a) {
-  for_each_unit<true>(a.offsets, a.costoff, a.nbins, a.nunits, a.work,
+  for_each_unit<true>(a.offsets, a.costoff, a.nbins, a.bin_lo, a.bin_hi, a.nunits, a.work,
                       [&](uint32_t beg, uint32_t end) { degrid_range<T, NT>(a, beg, end); });
 }
 
@@ -300,23 +300,27 @@ cudaError_t launch_degrid_v2(wp_ctx* ctx, const float2* grid, float2* out, const
   a.work = ctx->d_work + 2;
   cudaError_t e;
   if ((e = launch_bin_costs(ctx, s))) return e;
-  const bool small = *std::max_element(ctx->supp.begin(), ctx->supp.end()) <= kSmallMaxS;
-  auto run = [&](auto kern, int threads) -> cudaError_t {
+  // the planes of support <= 16 (a prefix of the bins) in the 32-warp shape, the rest in 16 warps
+  const int64_t split = small_planes_end(ctx) * ctx->geo.ntiles;
+  auto run = [&](auto kern, int threads, int64_t lo, int64_t hi) -> cudaError_t {
+    if (lo >= hi) return cudaSuccess;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err) return err;
+    a.bin_lo = lo;
+    a.bin_hi = hi;
+    ++ctx->launches;
     kern<<<ctx->nsm, threads, smem, s>>>(a);
     return cudaGetLastError();
   };
+  auto both = [&](auto small_kern, auto large_kern) -> cudaError_t {
+    cudaError_t err = run(small_kern, kDegridThreadsSmall, 0, split);
+    if (err) return err;
+    return run(large_kern, kDegridThreadsLarge, split, ctx->nbins);
+  };
   switch (ctx->prm.table_type) {
-    case WP_TABLE_F16:
-      return small ? run(k_degrid_v2<__half2, kDegridThreadsSmall>, kDegridThreadsSmall)
-                   : run(k_degrid_v2<__half2, kDegridThreadsLarge>, kDegridThreadsLarge);
-    case WP_TABLE_BF16:
-      return small ? run(k_degrid_v2<BfWord, kDegridThreadsSmall>, kDegridThreadsSmall)
-                   : run(k_degrid_v2<BfWord, kDegridThreadsLarge>, kDegridThreadsLarge);
-    default:
-      return small ? run(k_degrid_v2<float2, kDegridThreadsSmall>, kDegridThreadsSmall)
-                   : run(k_degrid_v2<float2, kDegridThreadsLarge>, kDegridThreadsLarge);
+    case WP_TABLE_F16: return both(k_degrid_v2<__half2, kDegridThreadsSmall>, k_degrid_v2<__half2, kDegridThreadsLarge>);
+    case WP_TABLE_BF16: return both(k_degrid_v2<BfWord, kDegridThreadsSmall>, k_degrid_v2<BfWord, kDegridThreadsLarge>);
+    default: return both(k_degrid_v2<float2, kDegridThreadsSmall>, k_degrid_v2<float2, kDegridThreadsLarge>);
   }
 }
 

@@ -202,10 +202,10 @@ cudaError_t degrid_typed(wp_ctx* ctx, const float2* grid, float2* out, const uin
 }  // namespace
 
 cudaError_t launch_grid(wp_ctx* ctx, float2* grid, cudaStream_t s) {
-  ++ctx->launches;
-  bool used = false;
+  bool used = false;                       // the warp kernels count their own launches (one or two)
   const cudaError_t e = launch_grid_v2(ctx, grid, s, &used);
   if (e != cudaSuccess || used) return e;
+  ++ctx->launches;
   switch (ctx->prm.table_type) {
     case WP_TABLE_F16: return grid_typed<__half2>(ctx, grid, s);
     case WP_TABLE_BF16: return grid_typed<BfWord>(ctx, grid, s);
@@ -214,10 +214,10 @@ cudaError_t launch_grid(wp_ctx* ctx, float2* grid, cudaStream_t s) {
 }
 
 cudaError_t launch_degrid(wp_ctx* ctx, const float2* grid, float2* out, const uint32_t* index, cudaStream_t s) {
-  ++ctx->launches;
-  bool used = false;
+  bool used = false;                       // the warp kernels count their own launches (one or two)
   const cudaError_t e = launch_degrid_v2(ctx, grid, out, index, s, &used);
   if (e != cudaSuccess || used) return e;
+  ++ctx->launches;
   switch (ctx->prm.table_type) {
     case WP_TABLE_F16: return degrid_typed<__half2>(ctx, grid, out, index, s);
     case WP_TABLE_BF16: return degrid_typed<BfWord>(ctx, grid, out, index, s);

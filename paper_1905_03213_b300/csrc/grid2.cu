@@ -45,6 +45,7 @@ struct G2Args {
   int smem_bytes;           // dynamic shared memory of the launch
   int group_tiles;          // origin tiles of one tile row sorted as one segment, at most
   int nunits;               // work units (equal shares of the estimated work)
+  int64_t bin_lo, bin_hi;   // the bins this launch grids (a prefix or suffix of the planes)
   uint32_t* work;           // [2]: next unit, finished CTAs (both zero between launches)
 };
 
@@ -56,7 +57,6 @@ struct G2Args {
 // 2% faster than 24.
 constexpr int kGridThreadsSmall = 1024;
 constexpr int kGridThreadsLarge = 512;
-constexpr int kSmallMaxS = 16;
 constexpr int kRingRecs = 64;                  // a group: two records per lane
 constexpr int kRingBytes = kRingRecs * (16 + 8);
 __host__ __device__ constexpr int rings_bytes(int threads) { return threads / 32 * kRingBytes; }
@@ -324,7 +324,7 @@ __device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end, int& cur
 template <class T, int NT>
 __global__ void __launch_bounds__(NT, 1) k_grid_v2(G2Args a) {
   int cur_plane = -1;
-  for_each_unit<true>(a.offsets, a.costoff, a.nbins, a.nunits, a.work,
+  for_each_unit<true>(a.offsets, a.costoff, a.nbins, a.bin_lo, a.bin_hi, a.nunits, a.work,
                       [&](uint32_t beg, uint32_t end) { grid_range<T, NT>(a, beg, end, cur_plane); });
 }
 
@@ -455,23 +455,28 @@ cudaError_t launch_grid_v2(wp_ctx* ctx, float2* grid, cudaStream_t s, bool* used
   a.work = ctx->d_work;
   cudaError_t e;
   if ((e = launch_bin_costs(ctx, s))) return e;
-  const bool small = *std::max_element(ctx->supp.begin(), ctx->supp.end()) <= kSmallMaxS;
-  auto run = [&](auto kern, int threads) -> cudaError_t {
+  // Supports grow with the plane, so the planes of support <= 16 are a prefix of the bins: they
+  // run in the 32-warp shape, the planes of larger support in a second, 16-warp launch.
+  const int64_t split = small_planes_end(ctx) * ctx->geo.ntiles;
+  auto run = [&](auto kern, int threads, int64_t lo, int64_t hi) -> cudaError_t {
+    if (lo >= hi) return cudaSuccess;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err) return err;
+    a.bin_lo = lo;
+    a.bin_hi = hi;
+    ++ctx->launches;
     kern<<<ctx->nsm, threads, smem, s>>>(a);
     return cudaGetLastError();
   };
+  auto both = [&](auto small_kern, auto large_kern) -> cudaError_t {
+    cudaError_t err = run(small_kern, kGridThreadsSmall, 0, split);
+    if (err) return err;
+    return run(large_kern, kGridThreadsLarge, split, ctx->nbins);
+  };
   switch (ctx->prm.table_type) {
-    case WP_TABLE_F16:
-      return small ? run(k_grid_v2<__half2, kGridThreadsSmall>, kGridThreadsSmall)
-                   : run(k_grid_v2<__half2, kGridThreadsLarge>, kGridThreadsLarge);
-    case WP_TABLE_BF16:
-      return small ? run(k_grid_v2<BfWord, kGridThreadsSmall>, kGridThreadsSmall)
-                   : run(k_grid_v2<BfWord, kGridThreadsLarge>, kGridThreadsLarge);
-    default:
-      return small ? run(k_grid_v2<float2, kGridThreadsSmall>, kGridThreadsSmall)
-                   : run(k_grid_v2<float2, kGridThreadsLarge>, kGridThreadsLarge);
+    case WP_TABLE_F16: return both(k_grid_v2<__half2, kGridThreadsSmall>, k_grid_v2<__half2, kGridThreadsLarge>);
+    case WP_TABLE_BF16: return both(k_grid_v2<BfWord, kGridThreadsSmall>, k_grid_v2<BfWord, kGridThreadsLarge>);
+    default: return both(k_grid_v2<float2, kGridThreadsSmall>, k_grid_v2<float2, kGridThreadsLarge>);
   }
 }
 
@@ -519,6 +524,8 @@ void grid_job_desc(wp_ctx* ctx, float2* grid, size_t smem, void* out) {
   a.smem_bytes = (int)smem;
   a.group_tiles = group;
   a.nunits = 0;
+  a.bin_lo = 0;
+  a.bin_hi = ctx->nbins;
   a.work = nullptr;
   memcpy(out, &a, sizeof(a));
 }

@@ -18,6 +18,7 @@ constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxS = 32;                                     // larger supports: baseline kernel
 constexpr int kMaxStagedS = 16;                               // larger: staged if it fits, else global
+constexpr int kSmallMaxS = 16;                                // supports of the 32-warp launch shape
 constexpr int kStagedChunk = 2048;                            // records left room for beside a large table
 constexpr int kMaxKeys = 4096;                                  // origins of one segment
 constexpr int kCountsBytes = ((kMaxKeys + 1) * 4 + 15) & ~15;  // shared-memory counters
@@ -76,6 +77,14 @@ struct Lay {
   static constexpr int HB = lay_half_bytes(S, E);
   static constexpr int CB = lay_class_bytes(S, E);
 };
+
+// The number of leading planes whose support is at most kSmallMaxS: their bins are the prefix
+// [0, end * ntiles) of the bin order, run in the 32-warp shape; the others in the 16-warp shape.
+inline int64_t small_planes_end(const wp_ctx* ctx) {
+  int64_t p = 0;
+  while (p < (int64_t)ctx->supp.size() && ctx->supp[(size_t)p] <= kSmallMaxS) ++p;
+  return p;
+}
 
 __device__ __forceinline__ unsigned char* dyn_smem() {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -321,18 +330,21 @@ __device__ __forceinline__ uint32_t segment_end(const uint32_t* __restrict__ off
 // kTapered: unit u covers [C (u / N)^2, C ((u + 1) / N)^2) instead, so the units taken first (the
 // highest u) are the largest, about twice the mean, and the last ones taken are small: the CTAs
 // finish within a small unit of each other.
+// Only the bins [bin_lo, bin_hi) are cut into units (a launch that grids part of the planes).
 template <bool kTapered = false, class Body>
 __device__ __forceinline__ void for_each_unit(const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ costoff,
-                                              int64_t nbins, int nunits, uint32_t* work, Body body) {
+                                              int64_t nbins, int64_t bin_lo, int64_t bin_hi, int nunits,
+                                              uint32_t* work, Body body) {
   __shared__ int unit;
-  const uint32_t total = offsets[nbins];
-  const uint32_t ctotal = costoff[nbins];
-  auto split = [&](uint64_t x) -> uint32_t {
+  const uint32_t total = offsets[bin_hi];
+  const uint32_t clo = costoff[bin_lo], chi = costoff[bin_hi];
+  const uint32_t ctotal = chi - clo;
+  auto split = [&](uint64_t x) -> uint32_t {        // x: cost position relative to clo
     if (x >= ctotal) return total;
-    const int64_t b = find_bin(costoff, nbins, (uint32_t)x);
+    const int64_t b = find_bin(costoff, nbins, clo + (uint32_t)x);
     const uint32_t c0 = costoff[b], cb = costoff[b + 1] - c0;
     const uint32_t n = offsets[b + 1] - offsets[b];
-    return offsets[b] + (uint32_t)(((uint64_t)(x - c0) * n) / cb);
+    return offsets[b] + (uint32_t)(((uint64_t)(clo + x - c0) * n) / cb);
   };
   for (;;) {
     if (threadIdx.x == 0) unit = nunits - 1 - (int)atomicAdd(&work[0], 1u);

@@ -370,3 +370,30 @@ def test_profile_counts_phases_and_launches(torch_cuda):
     wp.degrid_last(g)
     ms, cnt, launches = wp.profile_read()
     assert {k: v for k, v in cnt.items() if v} == {"degrid": 1} and launches == 5
+
+
+def test_supports_across_16_split_into_two_launches(torch_cuda):
+    """Planes of support <= 16 (a prefix of the bins) run in the 32-warp launch and the rest in
+    the 16-warp launch: both halves of one grid and one degridding against the oracle, and the
+    launch count shows the two launches."""
+    torch = torch_cuda
+    case = random_case(n=192, nrow=1500, nchan=2, n_w=9, s_min=8, s_max=24, seed=71, pairs=True)
+    sup = oracle.plane_supports(case.prm.n_w, case.prm.s_min, case.prm.s_max)
+    assert sup.min() <= 16 < sup.max()
+    wp = make_wproj(case)
+    uvw, f, vis, wt = to_dev(case)
+    wp.profile(True)
+    wp.profile_read()
+    g, _, _ = wp.grid(uvw, f, vis, wt, hermitian_pairs=True, keep_binning=True)
+    _, _, launches = wp.profile_read()
+    # 1 channel + 8 plan + 4 work-estimate scan + 2 gridding + 1 scalars
+    assert launches == 16
+    crd, g_ref, _ = oracle_results(case)
+    e, _ = peak_rel(g.cpu().numpy(), g_ref)
+    assert e < 1e-5, e
+    G = synth.random_grid(case.prm.n, 3)
+    pred = wp.degrid(uvw, f, torch.from_numpy(G).cuda()).cpu().numpy().ravel()
+    ref = oracle.degrid(oracle.coords(case.uvw, case.freqs, case.prm), G.astype(np.complex128), case.tables,
+                        case.prm, threads=4)
+    e2, _ = peak_rel(pred, ref)
+    assert e2 < 1e-5, e2
