@@ -369,40 +369,93 @@ def profiled_traffic(table: str, rows: int, config: str = "fp32"):
 
 
 def run_e2e(wp, uvw, vis, wt, freq, grid, sum_w, ndrop, pred, image, cfg, args, stream, units):
-    """The same step through the public API from pinned host buffers (copies inside the timing)."""
+    """The same step through the public API from pinned host buffers, every step's copies inside
+    the timing: each step copies its inputs (uvw, freq, vis, weight) host -> device and reads its
+    image back device -> host. Measured two ways: serially (copy, compute, read back, on one
+    stream), and as a stream pipeline with two device input sets, where step i + 1's copies (on a
+    copy stream) run while step i computes and step i's image is read back on a third stream."""
     import torch
     n = cfg.n
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dev = uvw.device
     h_uvw, h_vis, h_wt = uvw.cpu().pin_memory(), vis.cpu().pin_memory(), wt.cpu().pin_memory()
     h_freq = freq.cpu().pin_memory()
-    h_img = torch.empty((n, n), dtype=torch.float32).pin_memory()
-    d_uvw, d_vis, d_wt, d_freq = torch.empty_like(uvw), torch.empty_like(vis), torch.empty_like(wt), torch.empty_like(freq)
+    h_img = [torch.empty((n, n), dtype=torch.float32).pin_memory() for _ in range(2)]
+    sets = [(torch.empty_like(uvw), torch.empty_like(freq), torch.empty_like(vis), torch.empty_like(wt))
+            for _ in range(2)]
+    imgs = [image, torch.empty_like(image)]
 
-    def e2e_step():
-        d_uvw.copy_(h_uvw, non_blocking=True)
-        d_freq.copy_(h_freq, non_blocking=True)
-        d_vis.copy_(h_vis, non_blocking=True)
-        d_wt.copy_(h_wt, non_blocking=True)
+    def compute(x, img):
+        d_uvw, d_freq, d_vis, d_wt = x
         wp.make_wkernels()
         wp.grid(d_uvw, d_freq, d_vis, d_wt, grid=grid, sum_w=sum_w, n_dropped=ndrop,
                 hermitian_pairs=cfg.hermitian_pairs, keep_binning=True)
         wp.degrid_last(grid, vis_out=pred)
-        wp.fft_to_image(grid, sum_w, image=image)
-        h_img.copy_(image, non_blocking=True)
+        wp.fft_to_image(grid, sum_w, image=img)
 
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
+    def copy_in(x):
+        for d, h in zip(x, (h_uvw, h_freq, h_vis, h_wt)):
+            d.copy_(h, non_blocking=True)
+
+    # serial: one stream, copy in, compute, read back
+    def serial_step():
+        copy_in(sets[0])
+        compute(sets[0], imgs[0])
+        h_img[0].copy_(imgs[0], non_blocking=True)
+
     steps = max(2, args.steps // 2)
+    for _ in range(2):
+        serial_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
-        e2e_step()
+        serial_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_serial = e0.elapsed_time(e1) / steps
+
+    # pipelined: copy stream, compute stream (the current one), read-back stream
+    cs, rs = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    used = [torch.cuda.Event() for _ in range(2)]       # compute done with input set / image x
+    read = [torch.cuda.Event() for _ in range(2)]       # image x read back
+    for ev in used + read:
+        ev.record(stream)
+
+    def pipelined_step(i):
+        x = i % 2
+        cs.wait_event(used[x])                          # step i - 2 no longer reads set x
+        with torch.cuda.stream(cs):
+            copy_in(sets[x])
+        copied[x].record(cs)
+        stream.wait_event(copied[x])
+        stream.wait_event(read[x])                      # step i - 2's image x has been read back
+        compute(sets[x], imgs[x])
+        used[x].record(stream)
+        rs.wait_event(used[x])
+        with torch.cuda.stream(rs):
+            h_img[x].copy_(imgs[x], non_blocking=True)
+        read[x].record(rs)
+
+    for i in range(2):
+        pipelined_step(i)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    cs.wait_event(e0)
+    for i in range(steps):
+        pipelined_step(i)
+    stream.wait_event(read[0])
+    stream.wait_event(read[1])
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     h2d = h_uvw.numel() * 8 + h_vis.numel() * 8 + h_wt.numel() * 4 + h_freq.numel() * 8
     return {"value": units / (ms * 1e-3), "unit": "visibilities/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": h_img.numel() * 4, "ms_per_step": ms}
+            "d2h_bytes_per_step": h_img[0].numel() * 4, "ms_per_step": ms,
+            "mode": "pipelined: step i + 1's host-to-device copies overlap step i's compute (two device "
+                    "input sets, copy and read-back streams); every step's copies are inside the timing",
+            "serial": {"value": units / (ms_serial * 1e-3), "ms_per_step": ms_serial,
+                       "mode": "copy in, compute, read back, one stream"}}
 
 
 def cpu_sample_rows(cfg, target_vis):
