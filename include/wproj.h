@@ -82,7 +82,7 @@ typedef struct wp_params {
   int32_t device;       /* CUDA device ordinal */
   int32_t units_per_cta; /* schedule granularity of the gridding and degridding kernels: their
                             estimated work is cut into units_per_cta x (SM count) work units that
-                            persistent CTAs take from a counter; 1..64, 0 = default (6) */
+                            persistent CTAs take from a counter; 1..64, 0 = default (4) */
 } wp_params;
 
 /* Creates a context: validates `p`, derives the per-plane supports and w values, computes

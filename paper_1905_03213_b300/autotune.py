@@ -90,7 +90,7 @@ def tune(params: dict, uvw: torch.Tensor, freq: torch.Tensor, vis: torch.Tensor,
     if use_cache and key in _cache:
         return _cache[key]
     timings = {}
-    u0 = 6 if 6 in units else units[0]
+    u0 = 4 if 4 in units else units[0]             # the library's default
     for tile in tiles:
         if _valid_tile(params, tile):
             timings[(tuple(tile), u0)] = _time_config(params, tile, u0, u, freq, v, w, hermitian_pairs,

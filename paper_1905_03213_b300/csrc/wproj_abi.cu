@@ -235,7 +235,7 @@ int wp_create(wp_ctx** out, const wp_params* p) {
   ctx->prm = q;
   if (ctx->prm.tile_x == 0) ctx->prm.tile_x = 32;
   if (ctx->prm.tile_y == 0) ctx->prm.tile_y = 32;
-  if (ctx->prm.units_per_cta == 0) ctx->prm.units_per_cta = 6;
+  if (ctx->prm.units_per_cta == 0) ctx->prm.units_per_cta = 4;
   ctx->m = q.screen_m ? q.screen_m : std::max(65, 4 * q.support_max + 1);
   auto bail = [&](int code, const std::string& msg) {
     g_create_error = msg;

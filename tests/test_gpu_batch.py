@@ -143,12 +143,12 @@ def test_autotune_tile_and_schedule_granularity(torch_cuda):
     p = case.prm
     params = dict(n=p.n, cell=p.cell, n_w=p.n_w, w_max=p.w_max, support_min=p.s_min, support_max=p.s_max,
                   oversample=p.os, screen_m=p.m)
-    tiles, units = ((16, 16), (32, 32)), (2, 6, 16)
+    tiles, units = ((16, 16), (32, 32)), (2, 4, 16)
     best, timings = tune(params, uvw, f, vis, wt, hermitian_pairs=True, tiles=tiles, units=units, reps=2,
                          with_degrid=True, use_cache=False)
     assert best["tile"] in tiles and best["units_per_cta"] in units
     # every tile at the default granularity, then every granularity at the best tile
-    assert set(timings) >= {(t, 6) for t in tiles} | {(min(timings, key=timings.get)[0], u) for u in units}
+    assert set(timings) >= {(t, 4) for t in tiles} | {(min(timings, key=timings.get)[0], u) for u in units}
     assert all(t > 0 for t in timings.values())
     _, g_ref, _ = oracle_results(case)
     for un in (1, best["units_per_cta"], 64):
