@@ -58,7 +58,10 @@ struct G2Args {
 constexpr int kGridThreadsSmall = 1024;
 constexpr int kGridThreadsLarge = 512;
 constexpr int kRingRecs = 64;                  // a group: two records per lane
-constexpr int kRingBytes = kRingRecs * (16 + 8);
+// ... followed by the batch slots of a warp pair (S > 16: two [start, size] slots, used by the
+// pair's first warp's ring)
+constexpr int kPairSlot = kRingRecs * (16 + 8);
+constexpr int kRingBytes = kPairSlot + 16;
 __host__ __device__ constexpr int rings_bytes(int threads) { return threads / 32 * kRingBytes; }
 // Records a warp takes at a time (S <= 16): a guided size, the plane's remaining records over
 // twice the CTA's warps, rounded up to 32 and kept within [32, 256], so that batches shrink as the
@@ -146,7 +149,7 @@ __device__ __forceinline__ void decode_record(const uint4& r, int os, ulonglong2
 
 template <int S, class T, bool kGlobal>
 __device__ __forceinline__ void warp_grid(const G2Args& a, int tab_off, const unsigned char* gtab, int h, int ring_off,
-                                          uint32_t pe, uint32_t* next, uint32_t sbeg, uint32_t send) {
+                                          uint32_t pe, uint32_t* next) {
   using L = Lay<S, T>;
   const int lane = threadIdx.x & 31;
   const int g = lane / S, slot = lane - g * S;
@@ -160,24 +163,40 @@ __device__ __forceinline__ void warp_grid(const G2Args& a, int tab_off, const un
   float2* __restrict__ comp = a.comp;
   const uint32_t n = (uint32_t)a.g.n;
   const int os = a.g.os;
-  // batches: taken from the CTA's counter (next != nullptr), or the one static piece
+  // Batches from the CTA's counter, of a guided size: the plane's remaining records over twice
+  // the CTA's walkers (warps, or warp pairs for S > 16), rounded up to 32 and kept within
+  // [32, 256]. For S > 16 the two warps of a pair (row halves) walk the same batches: the first
+  // takes each from the counter into one of two slots, alternately, and both read it after the
+  // pair's named barrier (one barrier per batch: a slot is rewritten only after the other warp
+  // has passed the next barrier, so after it has read the slot). Both warps take the same
+  // batches in the same order, so they reach every barrier together.
+  uint32_t grabs = 0;
   auto grab = [&](uint32_t& b, uint32_t& e) {
-    if (next) {
-      uint32_t v = 0, want = 0;
-      if (lane == 0) {
-        const uint32_t cur = *(volatile uint32_t*)next;     // a lower bound of the next record
-        const uint32_t rem = cur < pe ? pe - cur : 0u;
-        want = min(kBatchMax, max(kBatchMin, (rem / (2u * (blockDim.x / 32u)) + 31u) & ~31u));
-        v = atomicAdd(next, want);
-      }
-      b = __shfl_sync(0xffffffffu, v, 0);
-      want = __shfl_sync(0xffffffffu, want, 0);
-      e = b < pe ? min(b + want, pe) : b;
-    } else {
-      b = sbeg;
-      e = send;
-      sbeg = send;
+    uint32_t v = 0, want = 0;
+    if (lane == 0 && h == 0) {
+      const uint32_t walkers = (blockDim.x / 32u) / L::H;  // warps, or warp pairs
+      const uint32_t cur = *(volatile uint32_t*)next;     // a lower bound of the next record
+      const uint32_t rem = cur < pe ? pe - cur : 0u;
+      want = min(kBatchMax, max(kBatchMin, (rem / (2u * walkers) + 31u) & ~31u));
+      v = atomicAdd(next, want);
     }
+    if constexpr (L::H > 1) {
+      const int pair = (int)(threadIdx.x >> 5) / L::H;
+      uint32_t* slot = (uint32_t*)(dyn_smem() + pair * L::H * kRingBytes + kPairSlot) + 2 * (grabs & 1u);
+      if (lane == 0 && h == 0) {
+        slot[0] = v;
+        slot[1] = want;
+      }
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + pair), "r"(32 * L::H) : "memory");
+      v = slot[0];
+      want = slot[1];
+      ++grabs;
+    } else {
+      v = __shfl_sync(0xffffffffu, v, 0);
+      want = __shfl_sync(0xffffffffu, want, 0);
+    }
+    b = v;
+    e = b < pe ? min(b + want, pe) : b;
   };
   uint32_t cb, ce, nb, ne;
   grab(cb, ce);
@@ -257,9 +276,8 @@ __device__ __forceinline__ void warp_grid(const G2Args& a, int tab_off, const un
 
 // The records [pb, pe) of plane p (support S) with the whole CTA: stage the plane's table
 // unless it is staged already (or too large: then its global copy is read), and walk the
-// records: for S <= 16 each warp takes guided batches from a counter, so that dense and
-// sparse regions even out; for S > 16 each pair of warps (one per row half) walks one
-// contiguous piece.
+// records: each warp (for S > 16 each pair of warps, one per row half) takes guided batches
+// from a counter, so that dense and sparse regions even out.
 template <int S, class T, int NT>
 __device__ __noinline__ void grid_plane(const G2Args& a, int p, bool stage, bool staged, uint32_t pb, uint32_t pe) {
   using L = Lay<S, T>;
@@ -272,18 +290,9 @@ __device__ __noinline__ void grid_plane(const G2Args& a, int p, bool stage, bool
   const unsigned char* gtab = staged ? nullptr : a.lanetab + a.lanetab_off[p];
   const int warp = threadIdx.x >> 5;
   const int ring_off = warp * kRingBytes;
-  uint32_t sbeg = 0, send = 0;
-  if constexpr (L::H > 1) {
-    constexpr int kPieces = NT / 32 / L::H;
-    const int piece = warp / L::H;
-    const uint32_t nrec = pe - pb;
-    sbeg = pb + (uint32_t)((uint64_t)nrec * piece / kPieces);
-    send = pb + (uint32_t)((uint64_t)nrec * (piece + 1) / kPieces);
-  }
-  uint32_t* ctr = L::H > 1 ? nullptr : &next;
   const int h = warp % L::H;
-  if (staged) warp_grid<S, T, false>(a, tab_off, nullptr, h, ring_off, pe, ctr, sbeg, send);
-  else warp_grid<S, T, true>(a, tab_off, gtab, h, ring_off, pe, ctr, sbeg, send);
+  if (staged) warp_grid<S, T, false>(a, tab_off, nullptr, h, ring_off, pe, &next);
+  else warp_grid<S, T, true>(a, tab_off, gtab, h, ring_off, pe, &next);
 }
 
 // cur_plane: the plane whose table is staged (-1: none), the same in every thread of the CTA.
