@@ -104,7 +104,7 @@ __device__ __forceinline__ void warp_degrid(int tab_off, const unsigned char* gt
                                             int sx0, int sy0, int rec_off, int beg, int end,
                                             float2* __restrict__ out) {
   using L = Lay<S, T>;
-  constexpr int NB = NT == kDegridThreadsSmall ? 8 : (L::R <= 5 ? 32 : (L::R <= 8 ? 16 : 8));
+  constexpr int NB = NT == kDegridThreadsSmall ? 8 : (L::R <= 5 ? 32 : 16);
   const int lane = threadIdx.x & 31;
   const int g = lane / S, slot = lane - g * S;
   // lanes beyond the layout read (zero-tap) cells of the half's first row
