@@ -402,7 +402,7 @@ def run_e2e(wp, uvw, vis, wt, freq, grid, sum_w, ndrop, pred, image, cfg, args, 
         compute(sets[0], imgs[0])
         h_img[0].copy_(imgs[0], non_blocking=True)
 
-    steps = max(2, args.steps // 2)
+    steps = max(6, args.steps // 2)                 # enough steps for the pipeline to fill and drain
     for _ in range(2):
         serial_step()
     torch.cuda.synchronize()
