@@ -194,25 +194,74 @@ __device__ __noinline__ void degrid_segment(const D2Args& a, int p, bool stage, 
 template <class T, int NT>
 __device__ void degrid_range(const D2Args& a, uint32_t beg, uint32_t end) {
   constexpr int kMaxSupp = NT == kDegridThreadsSmall ? kSmallMaxS : kMaxS;
+  const int lane = threadIdx.x & 31;
   int64_t bin = find_bin(a.offsets, a.nbins, beg);
   uint32_t pos = beg;
   int cur_plane = -1;
   const int tab_off = kDecodeScratch;          // the decode's prefix-sum scratch comes first
+  // Every warp runs this loop redundantly, once per segment, so its loads are taken off the
+  // segment's critical path: lane l holds the end offsets[wb + 1 + l] of bin wb + l for a window
+  // of 32 bins starting at wb (offsets[wb] <= pos), loaded before the previous segment's work.
+  int64_t wb = bin;
+  uint32_t wend = a.offsets[min(wb + 1 + lane, a.nbins)];
+  // the values that depend only on the plane, recomputed when it changes
+  int pl = -1, s = 0, sub_off = 0, rec_off = 0, cap = 0;
+  bool staged = false;
   while (pos < end) {
-    bin = advance_bin(a.offsets, bin, a.nbins, pos);
-    const int p = (int)(bin / a.g.ntiles);
-    const int64_t tile = bin - (int64_t)p * a.g.ntiles;
-    const int ty = (int)(tile / a.g.ntx), tx = (int)(tile - (int64_t)ty * a.g.ntx);
-    const int s = a.g.supp[p];
-    // tables of S > 16 are staged too when they leave room for the grid region and a chunk
-    const int tbytes = a.g.os * a.g.os * lay_class_bytes(s, TabElem<T>::E);
-    const int sbytes = sub_bytes(a.g.tile_x, a.g.tile_y, a.group_tiles, s);
-    const bool staged = s <= kMaxStagedS || tab_off + tbytes + sbytes + kStagedChunk * (int)sizeof(Record) <= a.smem_bytes;
-    const int sub_off = tab_off + (staged ? tbytes : 0);
-    const int rec_off = sub_off + sbytes;
-    const int cap = min(NT * decode_per(NT), (a.smem_bytes - rec_off) / (int)sizeof(Record));
+    // the bin containing pos: the first window bin whose end exceeds pos (offsets[nbins] > pos)
+    const unsigned past = __ballot_sync(0xffffffffu, wend > pos);
+    if (past) {
+      bin = wb + __ffs(past) - 1;
+    } else {
+      bin = advance_bin(a.offsets, wb + 32, a.nbins, pos);      // offsets[wb + 32] <= pos
+      wb = bin;
+      wend = a.offsets[min(wb + 1 + lane, a.nbins)];
+    }
+    // 32-bit multiply-high divisions (bins < 2^24)
+    const uint32_t b32 = (uint32_t)bin;
+    const int p = (int)a.g.div_ntiles.div(b32);
+    const uint32_t tile = b32 - (uint32_t)p * (uint32_t)a.g.ntiles;
+    const int ty = (int)a.g.div_ntx.div(tile), tx = (int)(tile - (uint32_t)ty * (uint32_t)a.g.ntx);
+    if (p != pl) {
+      pl = p;
+      s = a.g.supp[p];
+      // tables of S > 16 are staged too when they leave room for the grid region and a chunk
+      const int tbytes = a.g.os * a.g.os * lay_class_bytes(s, TabElem<T>::E);
+      const int sbytes = sub_bytes(a.g.tile_x, a.g.tile_y, a.group_tiles, s);
+      staged = s <= kMaxStagedS || tab_off + tbytes + sbytes + kStagedChunk * (int)sizeof(Record) <= a.smem_bytes;
+      sub_off = tab_off + (staged ? tbytes : 0);
+      rec_off = sub_off + sbytes;
+      cap = min(NT * decode_per(NT), (a.smem_bytes - rec_off) / (int)sizeof(Record));
+    }
+    // the segment: this bin, plus the following bins of the tile row while all their records
+    // fit one chunk (ends from the window when it holds them)
+    const int wo = (int)(bin - wb);
+    uint32_t bound[8];
+    if (wo + 8 <= 32) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) bound[k] = __shfl_sync(0xffffffffu, wend, wo + k);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) bound[k] = a.offsets[min(bin + k + 1, a.nbins)];
+    }
+    uint32_t seg_end = min(end, bound[0]);
     int ntiles = 1;
-    const uint32_t seg_end = segment_end(a.offsets, a.nbins, bin, tx, a.g.ntx, pos, end, cap, a.group_tiles, &ntiles);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+      if (ntiles == k && k < a.group_tiles && tx + k < a.g.ntx && seg_end < end) {
+        const uint32_t nxt = min(end, bound[k]);
+        if (nxt - pos <= (uint32_t)cap) {
+          seg_end = nxt;
+          ntiles = k + 1;
+        }
+      }
+    }
+    // the next window, loaded now and used after this segment's work (the next segment starts
+    // at bin + ntiles or later when seg_end is a bin end)
+    if (seg_end < end) {
+      wb = bin + ntiles;
+      wend = a.offsets[min(wb + 1 + lane, a.nbins)];
+    }
     const bool stage = staged && p != cur_plane;
     cur_plane = staged ? p : -1;                  // an unstaged segment's grid region overwrites the table
     const int x0 = tx * a.g.tile_x, y0 = ty * a.g.tile_y;

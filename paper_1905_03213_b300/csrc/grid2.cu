@@ -304,7 +304,7 @@ __device__ void grid_range(const G2Args& a, uint32_t beg, uint32_t end, int& cur
   const int tab_off = rings_bytes(NT);
   while (pos < end) {
     bin = advance_bin(a.offsets, bin, a.nbins, pos);
-    const int p = (int)(bin / a.g.ntiles);
+    const int p = (int)a.g.div_ntiles.div((uint32_t)bin);   // bins < 2^24
     const uint32_t pe = min(end, a.offsets[(int64_t)(p + 1) * a.g.ntiles]);
     const int s = a.g.supp[p];
     const int tbytes = a.g.os * a.g.os * lay_class_bytes(s, TabElem<T>::E);

@@ -54,6 +54,7 @@ struct Geometry {
   double wscale;        // (Nw - 1) / w_max, 0 if Nw == 1
   const int32_t* supp;  // [Nw] device
   FastDiv div_os, div_tx, div_ty;   // divisions by os, tile_x, tile_y
+  FastDiv div_ntiles, div_ntx;      // divisions of a bin index (< 2^24) by ntiles, of a tile by ntx
 };
 
 // Stored element of a WP_TABLE_BF16 kernel table: one 32-bit word per complex tap, read as

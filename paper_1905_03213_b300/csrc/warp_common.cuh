@@ -295,31 +295,6 @@ __device__ __forceinline__ int decode_chunk(const uint4* __restrict__ grecs, con
   return kept;
 }
 
-// The segment starting at record `pos` of bin `bin` (tile column tx): the bin, plus the
-// following bins of the same tile row while all their records still fit one chunk of `cap`
-// (sparse tiles are sorted together, dense ones alone), never beyond `end`.
-__device__ __forceinline__ uint32_t segment_end(const uint32_t* __restrict__ offsets, int64_t nbins, int64_t bin,
-                                                int tx, int ntx, uint32_t pos, uint32_t end, int cap,
-                                                int group_tiles, int* ntiles) {
-  uint32_t bound[8];                            // ends of this bin and the next 7 (independent loads)
-#pragma unroll
-  for (int k = 0; k < 8; ++k) bound[k] = offsets[min(bin + k + 1, nbins)];
-  uint32_t seg_end = min(end, bound[0]);
-  int nt = 1;
-#pragma unroll
-  for (int k = 1; k < 8; ++k) {
-    if (nt == k && k < group_tiles && tx + k < ntx && seg_end < end) {
-      const uint32_t nxt = min(end, bound[k]);
-      if (nxt - pos <= (uint32_t)cap) {
-        seg_end = nxt;
-        nt = k + 1;
-      }
-    }
-  }
-  *ntiles = nt;
-  return seg_end;
-}
-
 // Work units: unit u covers the estimated-work range [ctotal u / nunits, ctotal (u + 1) /
 // nunits). Cost position x maps to bin b (costoff[b] <= x < costoff[b+1]) and to the record
 // offsets[b] + (x - costoff[b]) / cost_b * count_b, a monotone map, so the units partition

@@ -297,6 +297,8 @@ int wp_create(wp_ctx** out, const wp_params* p) {
   g.div_os = wp::FastDiv::make((uint32_t)g.os);
   g.div_tx = wp::FastDiv::make((uint32_t)g.tile_x);
   g.div_ty = wp::FastDiv::make((uint32_t)g.tile_y);
+  g.div_ntiles = wp::FastDiv::make((uint32_t)g.ntiles);
+  g.div_ntx = wp::FastDiv::make((uint32_t)g.ntx);
   g.os_l = (double)q.oversample * ((double)q.n * q.cell_rad);
   g.wscale = q.n_w > 1 ? (double)(q.n_w - 1) / q.w_max : 0.0;
   ctx->nbins = g.ntiles * q.n_w;
