@@ -11,10 +11,11 @@
 //   * The grid region under the segment's footprints is staged in shared memory once per
 //     segment; lane (g, a) keeps the cells of its rows of footprint column a in registers
 //     (row pairs packed for f32x2 FMAs) and reloads them only when the origin changes.
-//   * Per record a lane multiplies its taps (the same planar table as gridding, 8-byte
-//     loads) with its cells into a partial sum; the partials of a batch of records are then
-//     reduced across the warp with a halving butterfly (about one shuffle per record and
-//     component), after which lane l holds visibility l of the batch and stores it.
+//   * Per record a lane multiplies its taps (the same tap layout as gridding, 4-byte loads)
+//     with its cells into a partial sum; the partials of a batch of records are then reduced
+//     across the warp with a halving butterfly (about one shuffle per record and component),
+//     after which each record's total sits in the lanes batch_record names and one of them
+//     stores it.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -9,11 +9,12 @@
 //   * The plan sorts each (plane, tile) bin's records by footprint origin (row j0, then column
 //     i0), so the records of one origin are contiguous. A CTA takes work units (shares of the
 //     estimated work) from a global counter, the most expensive end first; per plane inside a
-//     unit it stages the plane's table in shared memory and gives each warp one contiguous
-//     piece of the plane's records. There is no other CTA-wide step.
-//   * A warp streams its piece 32 records at a time: each lane loads one record (coalesced),
-//     decodes it into the warp's shared-memory ring (FMA operands, origin, class offset), and
-//     loads its record of the next group while the warp walks this one.
+//     unit it stages the plane's table in shared memory, and its warps (warp pairs for S > 16)
+//     take the plane's records in guided batches from a shared-memory counter. There is no
+//     other CTA-wide step.
+//   * A warp streams its batch 64 records at a time: each lane loads two records (coalesced),
+//     decodes them into the warp's shared-memory ring (FMA operands, origin, class offset), and
+//     loads its records of the next group while the warp walks this one.
 //   * The walk: all 32 lanes on the same record, so every branch is warp-uniform. Lane (g, a)
 //     holds rows g R .. g R + R - 1 of one footprint column in registers: the warp's registers
 //     are the S x S cells under the current origin. Records of the same origin accumulate in
